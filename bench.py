@@ -1,0 +1,449 @@
+#!/usr/bin/env python
+"""Benchmark of the BOBA hot path on the GB300.
+
+One step = one pass of the whole path over one synthetic graph resident in HBM:
+BOBA reorder (key init, first occurrence, rank, relabel), then the COO->CSR
+build of the reordered graph and ``--spmv-iters`` SpMV products y = A x.
+
+Printed (rank 0, one JSON line):
+  value        reorder throughput, Gedges/s = m / (device time of the reorder
+               phase), summed over all ranks (each rank reorders its own copy)
+  ms_per_step  device time of the whole step (reorder + CSR + SpMV)
+  e2e          the same metric through the public API with the inputs in
+               pinned host memory: H2D of src/dst, reorder, D2H of perm and
+               the relabelled edges, all inside the timed region
+  roofline     the step's dominant kernel: algorithmic bytes per launch over
+               its mean event-timed duration, against the measured HBM copy
+               bandwidth
+  cpu_baseline the CPU oracle (single-threaded C) on a bounded sample
+
+``--impl reference`` times the CPU oracle instead (the method has no other
+implementation to run), on the same workload, metric and unit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import platform
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = ("BOBA reorder Gedges/s + % HBM roofline (plain vs batched); "
+          "SpMV GB/s BOBA vs random")
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 512 << 20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_info():
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return model, os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+# algorithmic (compulsory) bytes per launch of each kernel
+# ---------------------------------------------------------------------------
+
+def algorithmic_bytes(m: int, n: int, nnz: int):
+    """Bytes each kernel must move to or from HBM at the least.
+
+    Arrays of n (or 2m-bit) words that fit in L2 between kernels are still
+    counted once where they are produced or consumed for the first time.
+    """
+    bitmap = (2 * m + 7) // 8
+    return {
+        "reorder.init": 4 * n + bitmap,            # write key, clear bitmap
+        "reorder.first": 8 * m + 4 * n,            # stream I ++ J, final keys
+        "reorder.mark": 4 * n + bitmap,            # read keys, bitmap
+        "reorder.scan": bitmap + bitmap // 8,      # read bitmap, write group prefix
+        "reorder.emit": 4 * n + 4 * n + 4 * n,     # keys in, label + perm out
+        "reorder.relabel": 16 * m + 4 * n,         # src,dst in; src_out,dst_out out; label
+        "csr.hist": 8 * m + 8 * n,
+        "spmv": 8 * nnz + 16 * n,
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid=None):
+        self.proc = None
+        self.uuid = device_uuid
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "100"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import synth
+    import paper_2306_10410_gb300 as boba
+    from paper_2306_10410_gb300 import build as bb
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    bb.build()
+    boba.load()
+
+    w = synth.WORKLOADS[args.workload]
+    m, n = w.m, w.n
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    # inputs: generated on the host into pinned memory, then made resident in HBM
+    src_h = torch.empty(m, dtype=torch.int32, pin_memory=True)
+    dst_h = torch.empty(m, dtype=torch.int32, pin_memory=True)
+    w.generate(out=(src_h.numpy(), dst_h.numpy()))
+    src = src_h.to(dev)
+    dst = dst_h.to(dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    label = torch.empty(n, dtype=torch.int32, device=dev)
+    so = torch.empty(m, dtype=torch.int32, device=dev)
+    do = torch.empty(m, dtype=torch.int32, device=dev)
+    ws_r = torch.empty(boba.boba_reorder_workspace_bytes(m, n), dtype=torch.uint8, device=dev)
+
+    have_csr = boba.boba_coo_to_csr_workspace_bytes(m, n) > 0
+    if have_csr:
+        row_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        col = torch.empty(m, dtype=torch.int32, device=dev)
+        val = torch.empty(m, dtype=torch.float32, device=dev)
+        ws_c = torch.empty(boba.boba_coo_to_csr_workspace_bytes(m, n), dtype=torch.uint8,
+                           device=dev)
+        ws_s = torch.empty(max(256, boba.boba_spmv_workspace_bytes(n, m)), dtype=torch.uint8,
+                           device=dev)
+        x = torch.from_numpy(synth.uniform_f32(n, seed=w.seed)).to(dev)
+        y = torch.empty(n, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def reorder():
+        boba.check(boba.boba_reorder_ex(src, dst, m, n, perm, so, do, label, ws_r,
+                                        ws_r.numel(), stream), "reorder")
+
+    def csr():
+        boba.check(boba.boba_coo_to_csr(so, do, m, n, row_ptr, col, val, ws_c, ws_c.numel(),
+                                        stream), "csr")
+
+    def spmv():
+        boba.check(boba.boba_spmv_csr(row_ptr, col, val, x, y, n, m, ws_s, ws_s.numel(),
+                                      stream), "spmv")
+
+    def step(ev):
+        ev[0].record(stream)
+        reorder()
+        ev[1].record(stream)
+        if have_csr:
+            csr()
+            ev[2].record(stream)
+            for _ in range(args.spmv_iters):
+                spmv()
+        ev[3].record(stream)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step([torch.cuda.Event(enable_timing=True) for _ in range(4)])
+    boba.stream_status(stream)
+
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    sampler = ClockSampler(f"GPU-{uuid}" if uuid else None)
+    sampler.start()
+    time.sleep(0.3)
+    evs = []
+    barrier()
+    with boba.kernel_timing() as kt:
+        for _ in range(args.steps):
+            flush.zero_()                       # L2 flush between steps (not timed)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            step(ev)
+            evs.append(ev)
+        barrier()
+    clocks = sampler.stop()
+    boba.stream_status(stream)
+
+    t_reorder = [e[0].elapsed_time(e[1]) for e in evs]
+    t_step = [e[0].elapsed_time(e[3]) for e in evs]
+    t_csr = [e[1].elapsed_time(e[2]) for e in evs] if have_csr else []
+    t_spmv = [e[2].elapsed_time(e[3]) for e in evs] if have_csr else []
+    reorder_ms = sum(t_reorder) / len(t_reorder)
+    step_ms = sum(t_step) / len(t_step)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([reorder_ms, step_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        reorder_ms, step_ms = t.tolist()
+    value = world * m / (reorder_ms * 1e-3) / 1e9
+
+    # per-kernel roofline
+    hbm, peak_kind = peaks()
+    alg = algorithmic_bytes(m, n, m)
+    kern = {}
+    for name, (tot_ms, launches) in kt.result.items():
+        mean_ms = tot_ms / max(1, launches)
+        a = alg.get(name)
+        gbs = (a / (mean_ms * 1e-3) / 1e9) if a else None
+        kern[name] = {"launches": launches, "mean_ms": round(mean_ms, 5),
+                      "share": None, "alg_bytes": a,
+                      "achieved_gbs": round(gbs, 1) if gbs else None,
+                      "frac": round(gbs / hbm, 4) if gbs else None}
+    tot_all = sum(v[0] for v in kt.result.values())
+    for name, (tot_ms, _) in kt.result.items():
+        kern[name]["share"] = round(tot_ms / tot_all, 4) if tot_all else None
+    dom = max(kt.result.items(), key=lambda kv: kv[1][0])[0] if kt.result else None
+    launches = sum(v[1] for v in kt.result.values())
+    traffic = load_traffic(dom, args.workload)
+    roof = None
+    if dom and kern[dom]["achieved_gbs"]:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": kern[dom]["achieved_gbs"],
+                "peak": hbm, "unit": "GB/s", "frac": kern[dom]["frac"], "traffic": traffic,
+                "peak_source": peak_kind}
+    full = 24 * m + 4 * n
+    reorder_roof = {"alg_bytes": full, "achieved_gbs": round(full / (reorder_ms * 1e-3) / 1e9, 1),
+                    "frac": round(full / (reorder_ms * 1e-3) / 1e9 / hbm, 4)}
+
+    # end-to-end through the public API with host buffers
+    e2e = run_e2e(args, boba, torch, dev, stream, src_h, dst_h, m, n, world)
+
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Gedges/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": w.name, "m": m, "n": n, "kind": w.kind, "seed": w.seed,
+                   "spmv_iters": args.spmv_iters if have_csr else 0,
+                   "l2": "flushed between steps (512 MiB write); inputs 8m bytes > L2",
+                   "parallelism": f"replicas x{world}"},
+        "phases_ms": {"reorder": round(reorder_ms, 4),
+                      "csr": round(statistics.mean(t_csr), 4) if t_csr else None,
+                      "spmv_total": round(statistics.mean(t_spmv), 4) if t_spmv else None},
+        "reorder_roofline": reorder_roof,
+        "roofline": roof,
+        "kernels": kern,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(w, args)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_e2e(args, boba, torch, dev, stream, src_h, dst_h, m, n, world):
+    """Same metric through the C ABI with the graph in pinned host memory."""
+    src_d = torch.empty(m, dtype=torch.int32, device=dev)
+    dst_d = torch.empty(m, dtype=torch.int32, device=dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    perm_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    so_h = torch.empty(m, dtype=torch.int32, pin_memory=True)
+    do_h = torch.empty(m, dtype=torch.int32, pin_memory=True)
+    ws = torch.empty(boba.boba_reorder_workspace_bytes(m, n), dtype=torch.uint8, device=dev)
+
+    def one(ev):
+        ev[0].record(stream)
+        src_d.copy_(src_h, non_blocking=True)
+        dst_d.copy_(dst_h, non_blocking=True)
+        boba.check(boba.boba_reorder_ex(src_d, dst_d, m, n, perm, src_d, dst_d, None, ws,
+                                        ws.numel(), stream), "reorder")
+        perm_h.copy_(perm, non_blocking=True)
+        so_h.copy_(src_d, non_blocking=True)
+        do_h.copy_(dst_d, non_blocking=True)
+        ev[1].record(stream)
+
+    for _ in range(max(1, args.warmup)):
+        one([torch.cuda.Event(enable_timing=True) for _ in range(2)])
+    torch.cuda.synchronize(dev)
+    times = []
+    steps = max(1, min(args.steps, 10))
+    for _ in range(steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        one(ev)
+        torch.cuda.synchronize(dev)
+        times.append(ev[0].elapsed_time(ev[1]))
+    boba.stream_status(stream)
+    ms = statistics.mean(times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+    return {"value": round(world * m / (ms * 1e-3) / 1e9, 3), "unit": "Gedges/s",
+            "ms_per_step": round(ms, 3), "h2d_bytes_per_step": 8 * m,
+            "d2h_bytes_per_step": 8 * m + 4 * n}
+
+
+def load_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if current."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return d.get(workload, {}).get(kernel)
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(w, m_sample):
+    # a prefix of the shuffled edge list is a uniform sample of its edges
+    return w.generate(edge_range=(0, m_sample))
+
+
+def time_oracle(I, J, n):
+    import oracle
+    t = time.perf_counter()
+    perm, label = oracle.boba_perm(I, J, n)
+    oracle.relabel(I, J, label, n)
+    return time.perf_counter() - t
+
+
+def cpu_baseline(w, args):
+    m_s = min(w.m, args.cpu_sample_edges)
+    I, J = oracle_sample(w, m_s)
+    times = [time_oracle(I, J, w.n) for _ in range(2)]
+    t = statistics.median(times)
+    model, cores = cpu_info()
+    return {"value": round(m_s / t / 1e9, 5), "unit": "Gedges/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {m_s} edges of {w.name} (n={w.n}), reorder (perm + relabel), "
+                      f"median of 2 runs; host {model}, {cores} cores visible, 1 used"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import synth
+    w = synth.WORKLOADS[args.workload]
+    m_s = min(w.m, args.cpu_sample_edges)
+    I, J = oracle_sample(w, m_s)
+    for _ in range(args.warmup):
+        time_oracle(I, J, w.n)
+    times = [time_oracle(I, J, w.n) for _ in range(args.steps)]
+    t = statistics.mean(times)
+    v = m_s / t / 1e9
+    model, cores = cpu_info()
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": "Gedges/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": w.name, "m": w.m, "n": w.n, "sample_edges": m_s},
+        "cpu_baseline": {"value": round(v, 5), "unit": "Gedges/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {m_s} edges of {w.name}, reorder (perm + relabel) "
+                                   f"per step; host {model}, {cores} cores visible, 1 used"},
+        "e2e": {"value": round(v, 5), "unit": "Gedges/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="rmat24_m2^28",
+                    help="one of: " + ", ".join(sorted(__import__("synth").WORKLOADS)))
+    ap.add_argument("--spmv-iters", type=int, default=20)
+    ap.add_argument("--cpu-sample-edges", type=int, default=1 << 27)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)        # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * boba.h -- C ABI of libboba.so, a GB300 (sm_103a) implementation of BOBA,
+ * "Batched Order By Attachment" (arXiv 2306.10410), the lightweight vertex
+ * reordering of COO edge lists, plus the CSR build and SpMV used to measure
+ * the locality it buys.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - A COO graph is two int32 arrays src (I) and dst (J) of length m; edge e
+ *    goes src[e] -> dst[e] (Sec. 2.1).  Vertex IDs are 0-based in [0, n).
+ *  - The endpoint stream is I ++ J: position i < m holds src[i], position
+ *    m + e holds dst[e] (Sec. 4.3).
+ *  - perm_out[k] = v means that new label k is old vertex v (p_k = v,
+ *    Sec. 4.3); label = perm^-1.
+ *  - Unless stated otherwise every pointer is a DEVICE pointer of the current
+ *    CUDA device, owned by the caller; the library never frees or retains it.
+ *    Arrays must not overlap unless an entry point says they may.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls only enqueue work: they return before the GPU finishes,
+ *    and a returned BOBA_OK means the arguments were accepted and the kernels
+ *    launched.  Errors found on the device (an ID outside [0, n), a spin-wait
+ *    that gave up) are recorded in a per-device status word that
+ *    boba_stream_status() reads; offending elements are skipped and never
+ *    cause an out-of-bounds access.
+ *  - Sizes above 2^31 - 1 (m, n, nnz) return BOBA_ERR_TOO_LARGE: keys are
+ *    32-bit positions in [0, 2m).
+ */
+#ifndef BOBA_H
+#define BOBA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum boba_status {
+    BOBA_OK = 0,
+    BOBA_ERR_INVALID_ARG = 1,      /* bad size, NULL pointer, misuse          */
+    BOBA_ERR_ID_OUT_OF_RANGE = 2,  /* a vertex ID outside [0, n) was skipped  */
+    BOBA_ERR_TOO_LARGE = 3,        /* m, n or nnz above 2^31 - 1              */
+    BOBA_ERR_WORKSPACE = 4,        /* workspace too small / cannot grow now   */
+    BOBA_ERR_TIMEOUT = 5,          /* a bounded device spin-wait gave up      */
+    BOBA_ERR_CUDA = 6              /* a CUDA runtime call failed              */
+} boba_status_t;
+
+/* ------------------------------------------------------------------------
+ * Reordering (Sec. 4.3 Alg. 1 and Sec. 4.5 Alg. 2 with an AtomicMin update)
+ * ------------------------------------------------------------------------ */
+
+/*
+ * boba_reorder -- the BOBA ordering of one COO graph and the relabelled edges.
+ *
+ * Computes, for every vertex v, key(v) = the lowest position at which v occurs
+ * in I ++ J (Alg. 2 with AtomicMin, Sec. 4.5, which the paper notes recovers
+ * the first-occurrence order of Alg. 1, Sec. 4.3), orders the vertices that
+ * occur by increasing key, and appends the vertices that occur in no edge in
+ * ascending original ID.  Then rewrites each edge through the new labels
+ * (Sec. 5.3): src_out[e] = label[src[e]], dst_out[e] = label[dst[e]]; edge
+ * order is kept.  The result is unique and is returned bit-exactly.
+ *
+ *   src, dst   int32[m]   input COO (device)
+ *   m          edges, 0 <= m <= 2^31 - 1
+ *   n          vertices, 0 <= n <= 2^31 - 1; n = 0 requires m = 0
+ *   perm_out   int32[n]   perm_out[new] = old (device)
+ *   src_out    int32[m]   relabelled sources; may alias src (device)
+ *   dst_out    int32[m]   relabelled destinations; may alias dst (device)
+ *
+ * Scratch memory comes from a workspace the library keeps per (device,
+ * stream) and grows on demand with cudaMalloc; growing is refused with
+ * BOBA_ERR_WORKSPACE while `stream` is being captured, so call once outside
+ * capture first.  Calls on the same stream are ordered and share that
+ * workspace; calls on different streams use different workspaces.
+ * An ID outside [0, n) is skipped (its output element is set to -1) and
+ * raises BOBA_ERR_ID_OUT_OF_RANGE in the status word.
+ */
+boba_status_t boba_reorder(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                           int32_t *perm_out, int32_t *src_out, int32_t *dst_out,
+                           void *stream);
+
+/*
+ * boba_reorder_workspace_bytes -- bytes of scratch boba_reorder_ex needs for
+ * a graph with m edges and n vertices (0 if the sizes are invalid).
+ */
+size_t boba_reorder_workspace_bytes(int64_t m, int64_t n);
+
+/*
+ * boba_reorder_ex -- boba_reorder with caller-owned scratch and extra outputs.
+ *
+ *   label_out  int32[n] or NULL: label_out[old] = new (perm^-1)
+ *   src_out, dst_out  may both be NULL: then only perm_out (and label_out)
+ *              are produced -- the permutation alone, which is the figure
+ *              the paper times (Sec. 1.2.4).  Giving one and not the other is
+ *              BOBA_ERR_INVALID_ARG.
+ *   ws         device scratch of at least boba_reorder_workspace_bytes(m, n)
+ *              bytes, 256-byte aligned; contents on entry are irrelevant;
+ *              must not be used by other work until this call's kernels end.
+ * Never allocates; safe to capture in a CUDA graph.
+ */
+boba_status_t boba_reorder_ex(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                              int32_t *perm_out, int32_t *src_out, int32_t *dst_out,
+                              int32_t *label_out, void *ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Batched reordering: G independent graphs in one persistent launch
+ * ------------------------------------------------------------------------ */
+
+/*
+ * boba_reorder_batched -- BOBA (as boba_reorder) for G independent graphs
+ * packed back to back, in one persistent kernel launch.
+ *
+ *   src, dst     int32[E]  packed COO, E = edge_off[G]; graph g owns edges
+ *                [edge_off[g], edge_off[g+1]) with LOCAL vertex IDs in
+ *                [0, vert_off[g+1] - vert_off[g])                   (device)
+ *   edge_off     int64[G+1], edge_off[0] = 0, non-decreasing          (device)
+ *   vert_off     int64[G+1], vert_off[0] = 0, non-decreasing          (device)
+ *   G            number of graphs, >= 0
+ *   max_m, max_n upper bounds on any one graph's edges and vertices, each
+ *                <= 2^31 - 1 (used only to validate and size scratch)
+ *   total_m, total_n  edge_off[G] and vert_off[G] (the host must know them to
+ *                size the outputs; they are not read back from the device)
+ *   perm_out     int32[total_n], packed by vert_off, local labels    (device)
+ *   src_out, dst_out int32[total_m], packed by edge_off, local labels; may
+ *                alias src, dst                                        (device)
+ *   ws, ws_bytes scratch of boba_reorder_batched_workspace_bytes(...) bytes
+ *
+ * The per-graph result equals boba_reorder on that graph alone, bit for bit.
+ * Offsets that are not monotone or exceed the totals raise
+ * BOBA_ERR_INVALID_ARG in the status word and the bad graphs are skipped.
+ * Never allocates; safe to capture in a CUDA graph.
+ */
+boba_status_t boba_reorder_batched(const int32_t *src, const int32_t *dst,
+                                   const int64_t *edge_off, const int64_t *vert_off,
+                                   int64_t G, int64_t max_m, int64_t max_n,
+                                   int64_t total_m, int64_t total_n,
+                                   int32_t *perm_out, int32_t *src_out, int32_t *dst_out,
+                                   void *ws, size_t ws_bytes, void *stream);
+
+size_t boba_reorder_batched_workspace_bytes(int64_t G, int64_t total_m, int64_t total_n);
+
+/* ------------------------------------------------------------------------
+ * Measurement path: COO -> CSR and SpMV (Alg. 3, Sec. 1.2.2)
+ * ------------------------------------------------------------------------ */
+
+/*
+ * boba_coo_to_csr -- pull CSR of a COO graph for Alg. 3: row v lists the
+ * in-neighbours of v, so rows come from dst and columns from src.  Entries of
+ * a row keep the input edge order (a stable sort by destination); duplicated
+ * edges stay separate.  The value of the entry for edge u -> v is
+ * fp32(1 / outdeg(u)), outdeg counting every edge leaving u.
+ *
+ *   src, dst   int32[m]             (device)
+ *   row_ptr    int64[n+1]           (device)
+ *   col_out    int32[m]             (device)
+ *   val_out    float[m]             (device)
+ *   ws         scratch of boba_coo_to_csr_workspace_bytes(m, n) bytes
+ * Never allocates; safe to capture in a CUDA graph.
+ */
+boba_status_t boba_coo_to_csr(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                              int64_t *row_ptr, int32_t *col_out, float *val_out,
+                              void *ws, size_t ws_bytes, void *stream);
+
+size_t boba_coo_to_csr_workspace_bytes(int64_t m, int64_t n);
+
+/*
+ * boba_spmv_csr -- y = A x for the CSR (row_ptr, col, val), Alg. 3 (pull),
+ * fp32 products and fp32 accumulation.  Rows are processed warp-per-row, or
+ * several short rows per warp, in a fixed order, so the result is the same
+ * run to run.  Rows longer than a threshold are split across warps whose
+ * partial sums are combined in a fixed order through the workspace.
+ *
+ *   row_ptr int64[n_rows+1], col int32[nnz], val float[nnz] (device);
+ *   x float[n_cols], y float[n_rows] (device; y must not alias x)
+ *   nnz       = row_ptr[n_rows] (the host must know it)
+ *   ws        scratch of boba_spmv_workspace_bytes(n_rows, nnz) bytes
+ * Never allocates; safe to capture in a CUDA graph.
+ */
+boba_status_t boba_spmv_csr(const int64_t *row_ptr, const int32_t *col, const float *val,
+                            const float *x, float *y, int64_t n_rows, int64_t nnz,
+                            void *ws, size_t ws_bytes, void *stream);
+
+size_t boba_spmv_workspace_bytes(int64_t n_rows, int64_t nnz);
+
+/* ------------------------------------------------------------------------
+ * Status
+ * ------------------------------------------------------------------------ */
+
+/*
+ * boba_stream_status -- synchronises `stream`, then returns and clears the
+ * status word of the current device: BOBA_OK, or the most severe error any
+ * kernel of this library recorded on this device since the last call (the
+ * word is per device, not per stream).  Returns BOBA_ERR_CUDA if the
+ * synchronisation itself failed.
+ */
+boba_status_t boba_stream_status(void *stream);
+
+/* boba_status_string -- a static, human-readable name for a status code. */
+const char *boba_status_string(boba_status_t status);
+
+/* boba_version -- a static version string of the library. */
+const char *boba_version(void);
+
+/* ------------------------------------------------------------------------
+ * Kernel timing (a measurement aid for the evaluation of Sec. 5)
+ * ------------------------------------------------------------------------ */
+
+/*
+ * boba_timing_enable -- on != 0: from now on every kernel this library
+ * launches is bracketed by two CUDA events recorded on the stream it is
+ * launched on, and its duration is accumulated under the kernel's name.
+ * Do not enable it while a stream is being captured into a CUDA graph.
+ * Off by default; costs one event pair per launch when on.
+ */
+void boba_timing_enable(int on);
+
+/*
+ * boba_timing_collect -- waits for every recorded event pair, folds the
+ * durations into per-kernel totals and returns the number of kernel names
+ * seen since the last reset (or -1 on a CUDA error).
+ */
+int boba_timing_collect(void);
+
+/* Name, total milliseconds and launch count of kernel record i (i < count). */
+const char *boba_timing_name(int i);
+double boba_timing_total_ms(int i);
+int64_t boba_timing_launches(int i);
+
+/* boba_timing_reset -- forget all totals and pending events. */
+void boba_timing_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BOBA_H */

@@ -1,0 +1,216 @@
+"""BOBA (Batched Order By Attachment, arXiv 2306.10410) on the NVIDIA GB300.
+
+Thin Python binding over the C ABI of ``include/boba.h`` (``libboba.so``).
+PyTorch supplies device memory and streams; every step of the computation runs
+in the library's CUDA kernels.  The functions named ``boba_*`` mirror the C
+entry points one to one (tensors in, argument marshalling only); the
+lower-case helpers allocate outputs and workspaces for convenience.
+"""
+from __future__ import annotations
+
+import torch
+
+from ._lib import BobaError, STATUS_NAMES, check, load
+
+__all__ = [
+    "BobaError", "load", "reorder", "reorder_perm", "coo_to_csr", "spmv", "stream_status",
+    "boba_reorder", "boba_reorder_ex", "boba_reorder_workspace_bytes", "boba_reorder_batched",
+    "boba_reorder_batched_workspace_bytes", "boba_coo_to_csr", "boba_coo_to_csr_workspace_bytes",
+    "boba_spmv_csr", "boba_spmv_workspace_bytes", "boba_stream_status", "boba_status_string",
+    "Workspace", "kernel_timing",
+]
+
+
+def _p(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libboba takes device tensors only")
+    if not t.is_contiguous():
+        raise ValueError("libboba takes contiguous tensors only")
+    return t.data_ptr()
+
+
+def _s(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _dt(t, dtype, name):
+    if t is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+
+
+# ---------------------------------------------------------------------------
+# raw C entry points (same names, same argument order)
+# ---------------------------------------------------------------------------
+
+def boba_reorder(src, dst, m, n, perm_out, src_out, dst_out, stream=None):
+    return load().boba_reorder(_p(src), _p(dst), m, n, _p(perm_out), _p(src_out), _p(dst_out),
+                               _s(stream))
+
+
+def boba_reorder_workspace_bytes(m, n):
+    return load().boba_reorder_workspace_bytes(m, n)
+
+
+def boba_reorder_ex(src, dst, m, n, perm_out, src_out, dst_out, label_out, ws, ws_bytes,
+                    stream=None):
+    return load().boba_reorder_ex(_p(src), _p(dst), m, n, _p(perm_out), _p(src_out),
+                                  _p(dst_out), _p(label_out), _p(ws), ws_bytes, _s(stream))
+
+
+def boba_reorder_batched(src, dst, edge_off, vert_off, G, max_m, max_n, total_m, total_n,
+                         perm_out, src_out, dst_out, ws, ws_bytes, stream=None):
+    return load().boba_reorder_batched(_p(src), _p(dst), _p(edge_off), _p(vert_off), G, max_m,
+                                       max_n, total_m, total_n, _p(perm_out), _p(src_out),
+                                       _p(dst_out), _p(ws), ws_bytes, _s(stream))
+
+
+def boba_reorder_batched_workspace_bytes(G, total_m, total_n):
+    return load().boba_reorder_batched_workspace_bytes(G, total_m, total_n)
+
+
+def boba_coo_to_csr(src, dst, m, n, row_ptr, col_out, val_out, ws, ws_bytes, stream=None):
+    return load().boba_coo_to_csr(_p(src), _p(dst), m, n, _p(row_ptr), _p(col_out),
+                                  _p(val_out), _p(ws), ws_bytes, _s(stream))
+
+
+def boba_coo_to_csr_workspace_bytes(m, n):
+    return load().boba_coo_to_csr_workspace_bytes(m, n)
+
+
+def boba_spmv_csr(row_ptr, col, val, x, y, n_rows, nnz, ws, ws_bytes, stream=None):
+    return load().boba_spmv_csr(_p(row_ptr), _p(col), _p(val), _p(x), _p(y), n_rows, nnz,
+                                _p(ws), ws_bytes, _s(stream))
+
+
+def boba_spmv_workspace_bytes(n_rows, nnz):
+    return load().boba_spmv_workspace_bytes(n_rows, nnz)
+
+
+def boba_stream_status(stream=None):
+    return load().boba_stream_status(_s(stream))
+
+
+def boba_status_string(code):
+    return load().boba_status_string(code).decode()
+
+
+# ---------------------------------------------------------------------------
+# convenience helpers
+# ---------------------------------------------------------------------------
+
+class Workspace:
+    """A reusable device scratch buffer (256-byte aligned, grown on demand)."""
+
+    def __init__(self, device=None):
+        self.device = torch.device("cuda") if device is None else torch.device(device)
+        self.buf = None
+
+    def get(self, nbytes: int) -> torch.Tensor:
+        nbytes = max(int(nbytes), 256)
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        return self.buf
+
+
+_default_ws = {}
+
+
+def _ws(ws, nbytes, device):
+    if ws is None:
+        key = (torch.device(device).index, torch.cuda.current_stream(device).cuda_stream)
+        ws = _default_ws.setdefault(key, Workspace(device))
+    return ws.get(nbytes)
+
+
+def stream_status(stream=None):
+    """Synchronise ``stream`` and raise BobaError if any kernel recorded an error."""
+    check(boba_stream_status(stream), "device status")
+
+
+def reorder(src, dst, n, *, perm_out=None, src_out=None, dst_out=None, label_out=None,
+            ws=None, stream=None):
+    """BOBA reorder of a COO graph on the GPU: returns (perm, src_out, dst_out).
+
+    ``src``/``dst`` are int32 CUDA tensors of length m with IDs in [0, n).
+    """
+    _dt(src, torch.int32, "src"); _dt(dst, torch.int32, "dst")
+    m = src.numel()
+    if dst.numel() != m:
+        raise ValueError("src and dst differ in length")
+    dev = src.device
+    perm_out = torch.empty(n, dtype=torch.int32, device=dev) if perm_out is None else perm_out
+    src_out = torch.empty_like(src) if src_out is None else src_out
+    dst_out = torch.empty_like(dst) if dst_out is None else dst_out
+    nbytes = boba_reorder_workspace_bytes(m, n)
+    buf = _ws(ws, nbytes, dev)
+    check(boba_reorder_ex(src, dst, m, n, perm_out, src_out, dst_out, label_out, buf,
+                          buf.numel(), stream), "boba_reorder_ex")
+    return perm_out, src_out, dst_out
+
+
+def reorder_perm(src, dst, n, *, perm_out=None, label_out=None, ws=None, stream=None):
+    """The permutation alone (no edge rewrite): returns perm (and fills label_out if given)."""
+    _dt(src, torch.int32, "src"); _dt(dst, torch.int32, "dst")
+    m = src.numel()
+    dev = src.device
+    perm_out = torch.empty(n, dtype=torch.int32, device=dev) if perm_out is None else perm_out
+    buf = _ws(ws, boba_reorder_workspace_bytes(m, n), dev)
+    check(boba_reorder_ex(src, dst, m, n, perm_out, None, None, label_out, buf, buf.numel(),
+                          stream), "boba_reorder_ex")
+    return perm_out
+
+
+def coo_to_csr(src, dst, n, *, row_ptr=None, col_out=None, val_out=None, ws=None, stream=None):
+    """Stable pull CSR (rows = dst, cols = src, val = 1/outdeg(src)): (row_ptr, col, val)."""
+    _dt(src, torch.int32, "src"); _dt(dst, torch.int32, "dst")
+    m = src.numel()
+    dev = src.device
+    row_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev) if row_ptr is None else row_ptr
+    col_out = torch.empty(m, dtype=torch.int32, device=dev) if col_out is None else col_out
+    val_out = torch.empty(m, dtype=torch.float32, device=dev) if val_out is None else val_out
+    buf = _ws(ws, boba_coo_to_csr_workspace_bytes(m, n), dev)
+    check(boba_coo_to_csr(src, dst, m, n, row_ptr, col_out, val_out, buf, buf.numel(), stream),
+          "boba_coo_to_csr")
+    return row_ptr, col_out, val_out
+
+
+def spmv(row_ptr, col, val, x, *, y=None, nnz=None, ws=None, stream=None):
+    """y = A x (fp32) for a CSR built by coo_to_csr."""
+    n_rows = row_ptr.numel() - 1
+    nnz = col.numel() if nnz is None else nnz
+    y = torch.empty(n_rows, dtype=torch.float32, device=x.device) if y is None else y
+    buf = _ws(ws, boba_spmv_workspace_bytes(n_rows, nnz), x.device)
+    check(boba_spmv_csr(row_ptr, col, val, x, y, n_rows, nnz, buf, buf.numel(), stream),
+          "boba_spmv_csr")
+    return y
+
+
+class kernel_timing:
+    """Context manager: per-kernel device time of every libboba launch inside it.
+
+    ``with kernel_timing() as kt: ...`` then ``kt.result`` maps kernel name ->
+    (total_ms, launches).  Events are recorded on each kernel's own stream.
+    """
+
+    def __enter__(self):
+        lib = load()
+        lib.boba_timing_reset()
+        lib.boba_timing_enable(1)
+        self.result = {}
+        return self
+
+    def __exit__(self, *exc):
+        lib = load()
+        lib.boba_timing_enable(0)
+        k = lib.boba_timing_collect()
+        if k < 0:
+            raise BobaError(6, "boba_timing_collect")
+        self.result = {lib.boba_timing_name(i).decode(): (lib.boba_timing_total_ms(i),
+                                                         int(lib.boba_timing_launches(i)))
+                       for i in range(k)}
+        lib.boba_timing_reset()
+        return False

@@ -1,0 +1,424 @@
+// BOBA reordering of one COO graph (arXiv 2306.10410, Sec. 4.3 and Sec. 4.5).
+//
+// Pipeline (all on one stream, no host synchronisation):
+//   k_init      key[v] = SENT; clear the rank bitmap and scan state
+//   k_first     key[v] = min position of v in I ++ J           (Alg. 2, AtomicMin)
+//   k_mark      bitmap bit key[v] := 1 for every vertex on an edge
+//   k_scan      exclusive popcount prefix of the bitmap, one word per 8 bitmap
+//               words, single pass with decoupled look-back
+//   k_emit      label[v] = rank of key[v] among finite keys, or, for a vertex on
+//               no edge, (#vertices on edges) + its rank among such vertices in
+//               ascending ID; perm[label[v]] = v                 (ParMapKeys)
+//   k_relabel   src_out[e] = label[src[e]], dst_out[e] = label[dst[e]]
+//
+// The ranks come from the bitmap of first-occurrence positions: bit i is set
+// iff position i of I ++ J is the first occurrence of its vertex, which is the
+// flag key[I[i]] == i of the method, built from the n keys instead of a second
+// pass over the 2m positions.
+#include <cstdio>
+
+#include "common.cuh"
+#include "host.hpp"
+#include "reorder_kernels.cuh"
+
+namespace boba {
+
+// ---------------------------------------------------------------------------
+// k_init: key[v] = SENT (Alg. 2's r = infinity^n); zero the bitmap, the
+// look-back state and the counters (one contiguous region of the workspace).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_init(uint32_t *__restrict__ key, int64_t n4,
+                                              uint32_t *__restrict__ zero, int64_t nzero)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint4 sent = make_uint4(kSent, kSent, kSent, kSent);
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    uint4 *k4 = reinterpret_cast<uint4 *>(key);
+    uint4 *z4 = reinterpret_cast<uint4 *>(zero);
+    for (int64_t i = t0; i < n4 / 4; i += stride) k4[i] = sent;
+    for (int64_t i = t0; i < nzero / 4; i += stride) z4[i] = z;
+}
+
+// ---------------------------------------------------------------------------
+// k_first: for every position i of I ++ J, key[(I++J)[i]] = min(key, i).
+// Alg. 2 (Sec. 4.5) with its update made an AtomicMin, which the paper notes
+// yields exactly the lowest position (the order of Alg. 1).
+// Work order: the grid sweeps the stream from position 0 upwards in chunks of
+// kFirstBlock*kFirstUnroll int4 loads per block, so by the time a position is
+// read most earlier positions are already recorded and the filtering read
+// (key[v] <= i) skips the atomic.
+// ---------------------------------------------------------------------------
+template <bool VEC>
+__global__ void __launch_bounds__(kFirstBlock) k_first(const int32_t *__restrict__ src,
+                                                       const int32_t *__restrict__ dst, int64_t m,
+                                                       uint32_t n, uint32_t *key, uint32_t *status)
+{
+    constexpr int U = kFirstUnroll;
+    const int64_t Q = VEC ? (m >> 2) : 0;   // full int4 quads per half
+    if (VEC) {
+        const int64_t total = 2 * Q;
+        const int64_t chunk = (int64_t)kFirstBlock * U;
+        const int64_t step = (int64_t)gridDim.x * chunk;
+        for (int64_t base = (int64_t)blockIdx.x * chunk; base < total; base += step) {
+            int4 q[U];
+            uint32_t p0[U];
+            bool ok[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t g = base + u * kFirstBlock + threadIdx.x;
+                ok[u] = g < total;
+                if (ok[u]) {
+                    const bool hi = g >= Q;
+                    const int64_t qi = hi ? g - Q : g;
+                    q[u] = ld_stream(reinterpret_cast<const int4 *>(hi ? dst : src) + qi);
+                    p0[u] = (uint32_t)((hi ? m : 0) + 4 * qi);
+                } else {
+                    q[u] = make_int4(0, 0, 0, 0);
+                    p0[u] = 0;
+                }
+            }
+            uint32_t cur[U][4];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int32_t v = comp(q[u], j);
+                    cur[u][j] = (ok[u] && (uint32_t)v < n) ? key[v] : 0u;
+                }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (!ok[u]) continue;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int32_t v = comp(q[u], j);
+                    if ((uint32_t)v >= n) raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE);
+                    else first_update(v, p0[u] + (uint32_t)j, cur[u][j], key);
+                }
+            }
+        }
+    }
+    // elements not covered by whole quads (all of them when !VEC)
+    const int64_t rem = m - 4 * Q;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 2 * rem; t += stride) {
+        const bool hi = t >= rem;
+        const int64_t e = 4 * Q + (hi ? t - rem : t);
+        const int32_t v = ld_stream((hi ? dst : src) + e);
+        const uint32_t pos = (uint32_t)((hi ? m : 0) + e);
+        if ((uint32_t)v >= n) raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE);
+        else first_update(v, pos, key[v], key);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_mark: set bit key[v] of the first-occurrence bitmap for each vertex on an
+// edge.  Keys are distinct positions, so bits never collide; words do, hence
+// the atomic OR.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_mark(const uint32_t *__restrict__ key, int64_t n4,
+                                              uint32_t *bitmap)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint4 *k4 = reinterpret_cast<const uint4 *>(key);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4 / 4; i += stride) {
+        const uint4 k = k4[i];
+        const uint32_t kk[4] = {k.x, k.y, k.z, k.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (kk[j] != kSent) atomicOr(&bitmap[kk[j] >> 5], 1u << (kk[j] & 31u));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_scan: exclusive prefix of the bitmap popcounts, one value per 8 words,
+// single pass with decoupled look-back.  The last tile stores the total, the
+// number of vertices that lie on an edge.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kScanBlock) k_scan(const uint32_t *__restrict__ bitmap,
+                                                     uint32_t *__restrict__ grp, uint64_t *tstat,
+                                                     uint32_t *counters, int64_t tiles,
+                                                     uint32_t *status)
+{
+    __shared__ typename BlockScan<kScanBlock>::Smem sm;
+    __shared__ uint32_t s_tile;
+    __shared__ uint64_t s_prefix;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&counters[kCtrScanTicket], 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const uint4 *w = reinterpret_cast<const uint4 *>(bitmap) + (tile * kScanTileWords) / 4 +
+                     2 * threadIdx.x;
+    const uint4 a = w[0], b = w[1];
+    const uint32_t c = __popc(a.x) + __popc(a.y) + __popc(a.z) + __popc(a.w) + __popc(b.x) +
+                       __popc(b.y) + __popc(b.z) + __popc(b.w);
+    uint32_t tot;
+    const uint32_t ex = BlockScan<kScanBlock>::exclusive(c, &tot, sm);
+    if (threadIdx.x < 32) {
+        const uint64_t p = lookback_exclusive(tstat, tile, tot, status);
+        if (threadIdx.x == 0) s_prefix = p;
+    }
+    __syncthreads();
+    grp[tile * kScanBlock + threadIdx.x] = (uint32_t)(s_prefix + ex);
+    if (tile == tiles - 1 && threadIdx.x == 0) counters[kCtrTotal] = (uint32_t)(s_prefix + tot);
+}
+
+// ---------------------------------------------------------------------------
+// k_emit: ParMapKeys (Alg. 2): label[v] = rank of key[v]; a vertex on no edge
+// gets (#vertices on edges) + its rank among such vertices in ascending ID
+// (a look-back scan over vertex tiles); perm[label[v]] = v.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kEmitBlock) k_emit(const uint32_t *__restrict__ key, uint32_t n,
+                                                     const uint32_t *__restrict__ bitmap,
+                                                     const uint32_t *__restrict__ grp,
+                                                     int32_t *__restrict__ label,
+                                                     int32_t *__restrict__ perm, uint64_t *tstat,
+                                                     uint32_t *counters, bool label_vec,
+                                                     uint32_t *status)
+{
+    __shared__ typename BlockScan<kEmitBlock>::Smem sm;
+    __shared__ uint32_t s_tile;
+    __shared__ uint64_t s_prefix;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&counters[kCtrEmitTicket], 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t v0 = tile * kEmitTileVerts + 4 * (int64_t)threadIdx.x;
+    uint4 k4 = make_uint4(kSent, kSent, kSent, kSent);
+    if (v0 < (int64_t)n) k4 = *reinterpret_cast<const uint4 *>(key + v0);   // key padded to 4
+    const uint32_t kk[4] = {k4.x, k4.y, k4.z, k4.w};
+    uint32_t iso[4], c = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        iso[j] = (v0 + j < (int64_t)n && kk[j] == kSent) ? 1u : 0u;
+        c += iso[j];
+    }
+    uint32_t tot;
+    const uint32_t ex = BlockScan<kEmitBlock>::exclusive(c, &tot, sm);
+    if (threadIdx.x < 32) {
+        const uint64_t p = lookback_exclusive(tstat, tile, tot, status);
+        if (threadIdx.x == 0) s_prefix = p;
+    }
+    __syncthreads();
+    const uint32_t on_edges = counters[kCtrTotal];
+    uint32_t next_iso = on_edges + (uint32_t)s_prefix + ex;
+    int32_t lab[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (v0 + j >= (int64_t)n) { lab[j] = -1; continue; }
+        if (kk[j] == kSent) lab[j] = (int32_t)(next_iso++);
+        else lab[j] = (int32_t)rank_of_key(kk[j], bitmap, grp);
+        if ((uint32_t)lab[j] < n) perm[lab[j]] = (int32_t)(v0 + j);
+        else raise_status(status, BOBA_ERR_TIMEOUT);   // only after a failed look-back
+    }
+    if (label_vec && v0 + 3 < (int64_t)n) {
+        *reinterpret_cast<int4 *>(label + v0) = make_int4(lab[0], lab[1], lab[2], lab[3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (v0 + j < (int64_t)n) label[v0 + j] = lab[j];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_relabel: rewrite every edge through the labels (Sec. 5.3), edge order
+// kept.  src_out/dst_out may alias src/dst: each element is read before the
+// same thread writes it.
+// ---------------------------------------------------------------------------
+template <bool VEC>
+__global__ void __launch_bounds__(kRelabelBlock) k_relabel(const int32_t *src, const int32_t *dst,
+                                                           int64_t m, uint32_t n,
+                                                           const int32_t *__restrict__ label,
+                                                           int32_t *src_out, int32_t *dst_out,
+                                                           uint32_t *status)
+{
+    constexpr int U = kRelabelUnroll;
+    const int64_t Q = VEC ? (m >> 2) : 0;
+    if (VEC) {
+        const int64_t total = 2 * Q;
+        const int64_t chunk = (int64_t)kRelabelBlock * U;
+        const int64_t step = (int64_t)gridDim.x * chunk;
+        for (int64_t base = (int64_t)blockIdx.x * chunk; base < total; base += step) {
+            int4 q[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t g = base + u * kRelabelBlock + threadIdx.x;
+                if (g < total) {
+                    const bool hi = g >= Q;
+                    q[u] = ld_stream(reinterpret_cast<const int4 *>(hi ? dst : src) + (hi ? g - Q : g));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t g = base + u * kRelabelBlock + threadIdx.x;
+                if (g < total) {
+                    int4 r;
+                    int32_t *rr = &r.x;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int32_t v = comp(q[u], j);
+                        if ((uint32_t)v < n) rr[j] = __ldg(label + v);
+                        else { rr[j] = -1; raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE); }
+                    }
+                    q[u] = r;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t g = base + u * kRelabelBlock + threadIdx.x;
+                if (g < total) {
+                    const bool hi = g >= Q;
+                    st_stream(reinterpret_cast<int4 *>(hi ? dst_out : src_out) + (hi ? g - Q : g), q[u]);
+                }
+            }
+        }
+    }
+    const int64_t rem = m - 4 * Q;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < 2 * rem; t += stride) {
+        const bool hi = t >= rem;
+        const int64_t e = 4 * Q + (hi ? t - rem : t);
+        const int32_t v = (hi ? dst : src)[e];
+        int32_t r;
+        if ((uint32_t)v < n) r = __ldg(label + v);
+        else { r = -1; raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE); }
+        (hi ? dst_out : src_out)[e] = r;
+    }
+}
+
+boba_status_t launch_reorder(const ReorderArgs &a, int64_t n4, size_t nzero_u32,
+                             cudaStream_t stream)
+{
+    {
+        const int64_t work = cdiv((int64_t)((size_t)n4 > nzero_u32 ? (size_t)n4 : nzero_u32) / 4, 256);
+        const int g = persistent_grid((const void *)k_init, 256, work);
+        BOBA_TIMED("reorder.init", stream,
+                   k_init<<<g, 256, 0, stream>>>(a.key, n4, a.bitmap, (int64_t)nzero_u32));
+    }
+    if (a.m > 0) {
+        const bool vec = aligned16(a.src) && aligned16(a.dst);
+        const int64_t work = cdiv(2 * a.m, 4 * kFirstBlock * kFirstUnroll);
+        if (vec) {
+            const int g = persistent_grid((const void *)k_first<true>, kFirstBlock, work);
+            BOBA_TIMED("reorder.first", stream,
+                       k_first<true><<<g, kFirstBlock, 0, stream>>>(a.src, a.dst, a.m, a.n, a.key,
+                                                                   a.status));
+        } else {
+            const int g = persistent_grid((const void *)k_first<false>, kFirstBlock, work * 4);
+            BOBA_TIMED("reorder.first", stream,
+                       k_first<false><<<g, kFirstBlock, 0, stream>>>(a.src, a.dst, a.m, a.n, a.key,
+                                                                    a.status));
+        }
+        const int gm = persistent_grid((const void *)k_mark, 256, cdiv(n4 / 4, 256));
+        BOBA_TIMED("reorder.mark", stream, k_mark<<<gm, 256, 0, stream>>>(a.key, n4, a.bitmap));
+        BOBA_TIMED("reorder.scan", stream,
+                   k_scan<<<(unsigned)a.scan_tiles, kScanBlock, 0, stream>>>(
+                       a.bitmap, a.grp, a.tstat_scan, a.counters, a.scan_tiles, a.status));
+    }
+    BOBA_TIMED("reorder.emit", stream,
+               k_emit<<<(unsigned)a.emit_tiles, kEmitBlock, 0, stream>>>(
+                   a.key, a.n, a.bitmap, a.grp, a.label, a.perm, a.tstat_emit, a.counters,
+                   a.label_vec, a.status));
+    if (a.src_out && a.m > 0) {
+        const bool vec = aligned16(a.src) && aligned16(a.dst) && aligned16(a.src_out) &&
+                         aligned16(a.dst_out);
+        const int64_t work = cdiv(2 * a.m, 4 * kRelabelBlock * kRelabelUnroll);
+        if (vec) {
+            const int g = persistent_grid((const void *)k_relabel<true>, kRelabelBlock, work);
+            BOBA_TIMED("reorder.relabel", stream,
+                       k_relabel<true><<<g, kRelabelBlock, 0, stream>>>(
+                           a.src, a.dst, a.m, a.n, a.label, a.src_out, a.dst_out, a.status));
+        } else {
+            const int g = persistent_grid((const void *)k_relabel<false>, kRelabelBlock, work * 4);
+            BOBA_TIMED("reorder.relabel", stream,
+                       k_relabel<false><<<g, kRelabelBlock, 0, stream>>>(
+                           a.src, a.dst, a.m, a.n, a.label, a.src_out, a.dst_out, a.status));
+        }
+    }
+    BOBA_LAUNCH_CHECK();
+    return BOBA_OK;
+}
+
+}  // namespace boba
+
+namespace boba {
+
+struct ReorderLayout {
+    int64_t n4, nwords, ngroups, scan_tiles, emit_tiles;
+    size_t key, label, grp, zero_begin, bitmap, tstat_scan, tstat_emit, counters, zero_end, total;
+};
+
+static bool reorder_layout(int64_t m, int64_t n, ReorderLayout &L)
+{
+    if (m < 0 || n < 0 || m > kMaxSize || n > kMaxSize) return false;
+    L.n4 = align_up((size_t)(n > 0 ? n : 1), 4);
+    L.nwords = (int64_t)align_up((size_t)cdiv(2 * m, 32) > 0 ? (size_t)cdiv(2 * m, 32) : 1,
+                                 kScanTileWords);
+    L.ngroups = L.nwords / 8;
+    L.scan_tiles = L.nwords / kScanTileWords;
+    L.emit_tiles = cdiv(n > 0 ? n : 1, kEmitTileVerts);
+    Carve c;
+    L.key = c.take(L.n4 * 4);
+    L.label = c.take(L.n4 * 4);
+    L.grp = c.take(L.ngroups * 4);
+    L.zero_begin = c.off;
+    L.bitmap = c.take(L.nwords * 4);
+    L.tstat_scan = c.take(L.scan_tiles * 8);
+    L.tstat_emit = c.take(L.emit_tiles * 8);
+    L.counters = c.take(kNumCounters * 4);
+    L.zero_end = c.off;
+    L.total = c.off;
+    return true;
+}
+
+}  // namespace boba
+
+using namespace boba;
+
+extern "C" size_t boba_reorder_workspace_bytes(int64_t m, int64_t n)
+{
+    ReorderLayout L;
+    if (!reorder_layout(m, n, L)) return 0;
+    return L.total;
+}
+
+extern "C" boba_status_t boba_reorder_ex(const int32_t *src, const int32_t *dst, int64_t m,
+                                         int64_t n, int32_t *perm_out, int32_t *src_out,
+                                         int32_t *dst_out, int32_t *label_out, void *ws,
+                                         size_t ws_bytes, void *stream_)
+{
+    if (m < 0 || n < 0) return BOBA_ERR_INVALID_ARG;
+    if (m > kMaxSize || n > kMaxSize) return BOBA_ERR_TOO_LARGE;
+    if (n == 0 && m > 0) return BOBA_ERR_INVALID_ARG;
+    if ((src_out == nullptr) != (dst_out == nullptr)) return BOBA_ERR_INVALID_ARG;
+    if (n == 0) return BOBA_OK;
+    if (perm_out == nullptr || ws == nullptr) return BOBA_ERR_INVALID_ARG;
+    if (m > 0 && (src == nullptr || dst == nullptr)) return BOBA_ERR_INVALID_ARG;
+    ReorderLayout L;
+    reorder_layout(m, n, L);
+    if (ws_bytes < L.total || !aligned256(ws)) return BOBA_ERR_WORKSPACE;
+    const DeviceInfo *dev = device_info();
+    if (!dev) return BOBA_ERR_CUDA;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+
+    char *base = static_cast<char *>(ws);
+    ReorderArgs a;
+    a.src = src;
+    a.dst = dst;
+    a.m = m;
+    a.n = (uint32_t)n;
+    a.key = reinterpret_cast<uint32_t *>(base + L.key);
+    a.label = label_out ? label_out : reinterpret_cast<int32_t *>(base + L.label);
+    a.perm = perm_out;
+    a.bitmap = reinterpret_cast<uint32_t *>(base + L.bitmap);
+    a.grp = reinterpret_cast<uint32_t *>(base + L.grp);
+    a.tstat_scan = reinterpret_cast<uint64_t *>(base + L.tstat_scan);
+    a.tstat_emit = reinterpret_cast<uint64_t *>(base + L.tstat_emit);
+    a.counters = reinterpret_cast<uint32_t *>(base + L.counters);
+    a.nwords = L.nwords;
+    a.scan_tiles = L.scan_tiles;
+    a.emit_tiles = L.emit_tiles;
+    a.status = dev->status;
+    a.src_out = src_out;
+    a.dst_out = dst_out;
+    a.label_vec = aligned16(a.label);
+    return launch_reorder(a, L.n4, (L.zero_end - L.zero_begin) / 4, stream);
+}

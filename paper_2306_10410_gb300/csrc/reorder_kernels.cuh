@@ -1,0 +1,74 @@
+// Device building blocks of the BOBA reordering, shared by the single-graph
+// path and the batched path.
+#pragma once
+
+#include "common.cuh"
+
+namespace boba {
+
+constexpr int kFirstBlock = 256;        // threads per block, first-occurrence pass
+constexpr int kFirstUnroll = 4;         // int4 loads in flight per thread
+constexpr int kRelabelBlock = 256;
+constexpr int kRelabelUnroll = 4;
+constexpr int kScanBlock = 256;
+constexpr int kScanTileWords = kScanBlock * 8;     // 8 bitmap words (one 32-byte sector) per thread
+constexpr int kEmitBlock = 256;
+constexpr int kEmitTileVerts = kEmitBlock * 4;     // 4 vertices (one int4 of keys) per thread
+constexpr int kNumCounters = 8;                    // tickets and totals in the workspace
+constexpr int kCtrScanTicket = 0, kCtrEmitTicket = 1, kCtrTotal = 2;
+
+struct ReorderArgs {
+    const int32_t *src, *dst;
+    int64_t m;
+    uint32_t n;
+    uint32_t *key;
+    int32_t *label;
+    int32_t *perm;
+    uint32_t *bitmap;       // nwords words, bit i = position i is a first occurrence
+    uint32_t *grp;          // exclusive popcount prefix, one per 8 bitmap words
+    uint64_t *tstat_scan, *tstat_emit;
+    uint32_t *counters;
+    int64_t nwords, scan_tiles, emit_tiles;
+    uint32_t *status;
+    int32_t *src_out, *dst_out;
+    bool label_vec;
+};
+
+// One position of I ++ J: lower key[v] to `pos` unless a position already
+// recorded for v is lower.  The filtering read may see a stale value: keys only
+// ever decrease, so a stale key is >= the current one and at worst costs an
+// atomic that changes nothing; the minimum itself is taken by atomicMin.
+__device__ __forceinline__ void first_update(int32_t v, uint32_t pos, uint32_t cur, uint32_t *key)
+{
+    if (cur > pos) atomicMin(&key[v], pos);
+}
+
+// Rank of a finite key among all first-occurrence positions: the popcount of
+// the bitmap below bit k.  grp[g] holds the count below word 8g; the eight
+// words of group g form one aligned 32-byte sector.
+__device__ __forceinline__ uint32_t rank_of_key(uint32_t k, const uint32_t *__restrict__ bitmap,
+                                                const uint32_t *__restrict__ grp)
+{
+    const uint32_t g = k >> 8;
+    const uint4 *gw = reinterpret_cast<const uint4 *>(bitmap) + 2 * (size_t)g;
+    const uint4 a = gw[0], b = gw[1];
+    const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    const uint32_t wi = (k >> 5) & 7u;
+    uint32_t r = grp[g];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if ((uint32_t)i < wi) r += __popc(w[i]);
+        else if ((uint32_t)i == wi) r += __popc(w[i] & ((1u << (k & 31u)) - 1u));
+    }
+    return r;
+}
+
+__device__ __forceinline__ int32_t comp(const int4 &q, int j)
+{
+    return j == 0 ? q.x : j == 1 ? q.y : j == 2 ? q.z : q.w;
+}
+
+boba_status_t launch_reorder(const ReorderArgs &a, int64_t n4, size_t nzero_u32,
+                             cudaStream_t stream);
+
+}  // namespace boba

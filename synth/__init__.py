@@ -51,9 +51,9 @@ def _load():
             lib = ctypes.CDLL(_LIB)
             u64, i64, p, ci, d = (ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p,
                                   ctypes.c_int, ctypes.c_double)
-            lib.synth_rmat.argtypes = [u64, ci, i64, i64, d, d, d, ci, ci, p, p, ci]
-            lib.synth_grid.argtypes = [u64, i64, ci, ci, p, p, ci]
-            lib.synth_er.argtypes = [u64, i64, i64, ci, ci, p, p, ci]
+            lib.synth_rmat.argtypes = [u64, ci, i64, i64, d, d, d, ci, ci, i64, i64, p, p, ci]
+            lib.synth_grid.argtypes = [u64, i64, ci, ci, i64, i64, p, p, ci]
+            lib.synth_er.argtypes = [u64, i64, i64, ci, ci, i64, i64, p, p, ci]
             lib.synth_permutation.argtypes = [u64, u64, i64, p]
             lib.synth_uniform_f32.argtypes = [u64, u64, i64, p]
             lib.synth_draws.argtypes = [u64, u64, i64, p]
@@ -81,37 +81,51 @@ def _alloc(m: int, out=None):
     return np.empty(m, dtype=np.int32), np.empty(m, dtype=np.int32)
 
 
+def _range(m, rng):
+    lo, hi = (0, m) if rng is None else (int(rng[0]), int(rng[1]))
+    if not 0 <= lo <= hi <= m:
+        raise ValueError("edge range outside [0, m]")
+    return lo, hi
+
+
 def rmat(scale: int, m: int, seed: int, n: int | None = None, abc=RMAT_ABC,
-         shuffle: bool = True, relabel: bool = True, out=None):
+         shuffle: bool = True, relabel: bool = True, out=None, edge_range=None):
     """Directed R-MAT COO (src, dst) int32 with ``n`` (default 2^scale) vertices.
 
     Duplicate edges and self-loops are kept.  ``out`` may pass preallocated
-    (e.g. pinned) int32 arrays of length >= m.
+    (e.g. pinned) int32 arrays.  ``edge_range=(lo, hi)`` produces only edges
+    [lo, hi) of the m-edge list (a prefix of the shuffled list is a uniform
+    sample of its edges).
     """
     n = (1 << scale) if n is None else int(n)
-    src, dst = _alloc(m, out)
+    lo, hi = _range(m, edge_range)
+    src, dst = _alloc(hi - lo, out)
     rc = _load().synth_rmat(seed, scale, n, m, abc[0], abc[1], abc[2], int(shuffle),
-                            int(relabel), _ptr(src), _ptr(dst), _threads())
+                            int(relabel), lo, hi, _ptr(src), _ptr(dst), _threads())
     if rc:
         raise ValueError("synth.rmat: bad arguments")
     return src, dst
 
 
-def grid(side: int, seed: int, shuffle: bool = True, relabel: bool = True, out=None):
+def grid(side: int, seed: int, shuffle: bool = True, relabel: bool = True, out=None,
+         edge_range=None):
     """4-neighbour side x side grid with both edge directions: m = 4 side (side-1)."""
     m = 4 * side * (side - 1)
-    src, dst = _alloc(m, out)
-    rc = _load().synth_grid(seed, side, int(shuffle), int(relabel), _ptr(src), _ptr(dst),
-                            _threads())
+    lo, hi = _range(m, edge_range)
+    src, dst = _alloc(hi - lo, out)
+    rc = _load().synth_grid(seed, side, int(shuffle), int(relabel), lo, hi, _ptr(src),
+                            _ptr(dst), _threads())
     if rc:
         raise ValueError("synth.grid: bad arguments")
     return src, dst
 
 
-def er(n: int, m: int, seed: int, shuffle: bool = True, relabel: bool = True, out=None):
+def er(n: int, m: int, seed: int, shuffle: bool = True, relabel: bool = True, out=None,
+       edge_range=None):
     """m edges with independent uniform endpoints in [0, n)."""
-    src, dst = _alloc(m, out)
-    rc = _load().synth_er(seed, n, m, int(shuffle), int(relabel), _ptr(src), _ptr(dst),
+    lo, hi = _range(m, edge_range)
+    src, dst = _alloc(hi - lo, out)
+    rc = _load().synth_er(seed, n, m, int(shuffle), int(relabel), lo, hi, _ptr(src), _ptr(dst),
                           _threads())
     if rc:
         raise ValueError("synth.er: bad arguments")
@@ -152,13 +166,13 @@ class Workload:
     scale: int = 0
     side: int = 0
 
-    def generate(self, out=None):
+    def generate(self, out=None, edge_range=None):
         if self.kind == "rmat":
-            return rmat(self.scale, self.m, self.seed, n=self.n, out=out)
+            return rmat(self.scale, self.m, self.seed, n=self.n, out=out, edge_range=edge_range)
         if self.kind == "grid":
-            return grid(self.side, self.seed, out=out)
+            return grid(self.side, self.seed, out=out, edge_range=edge_range)
         if self.kind == "er":
-            return er(self.n, self.m, self.seed, out=out)
+            return er(self.n, self.m, self.seed, out=out, edge_range=edge_range)
         raise ValueError(self.kind)
 
 

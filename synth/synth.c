@@ -91,7 +91,8 @@ typedef struct {
     int64_t n, m, side;
     int shuffle, relabel;
     feistel_t shuf, lab;
-    int32_t *src, *dst;
+    int32_t *src, *dst;      /* out[i - base] for output index i */
+    int64_t base;
     int64_t lo, hi;
 } job_t;
 
@@ -156,25 +157,27 @@ static void *run_job(void *arg)
             u = (int64_t)feistel_apply(&J->lab, (uint64_t)u);
             v = (int64_t)feistel_apply(&J->lab, (uint64_t)v);
         }
-        J->src[i] = (int32_t)u;
-        J->dst[i] = (int32_t)v;
+        J->src[i - J->base] = (int32_t)u;
+        J->dst[i - J->base] = (int32_t)v;
     }
     return NULL;
 }
 
-static int run_parallel(job_t *proto, int nthreads)
+static int run_parallel(job_t *proto, int64_t lo, int64_t hi, int nthreads)
 {
+    if (lo < 0 || hi > proto->m || lo > hi) return 1;
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 256) nthreads = 256;
-    if (proto->m < 65536) nthreads = 1;
+    if (hi - lo < 65536) nthreads = 1;
     job_t jobs[256];
     pthread_t th[256];
-    int64_t chunk = (proto->m + nthreads - 1) / nthreads;
+    int64_t chunk = (hi - lo + nthreads - 1) / nthreads;
     int started = 0;
+    proto->base = lo;
     for (int t = 0; t < nthreads; ++t) {
         jobs[t] = *proto;
-        jobs[t].lo = (int64_t)t * chunk;
-        jobs[t].hi = jobs[t].lo + chunk < proto->m ? jobs[t].lo + chunk : proto->m;
+        jobs[t].lo = lo + (int64_t)t * chunk;
+        jobs[t].hi = jobs[t].lo + chunk < hi ? jobs[t].lo + chunk : hi;
         if (jobs[t].lo >= jobs[t].hi) continue;
         if (nthreads == 1) { run_job(&jobs[t]); continue; }
         if (pthread_create(&th[started], NULL, run_job, &jobs[t]) != 0) {
@@ -203,8 +206,10 @@ static void common_init(job_t *J, uint64_t seed, int64_t n, int64_t m, int shuff
 }
 
 /* R-MAT on 2^scale IDs; IDs >= n are redrawn (n <= 2^scale).  Returns 0 / 1 bad arg. */
+/* Output edges [lo, hi) of the m-edge list go to src[0 .. hi-lo), dst[...]. */
 int synth_rmat(uint64_t seed, int scale, int64_t n, int64_t m, double a, double b, double c,
-               int shuffle, int relabel, int32_t *src, int32_t *dst, int nthreads)
+               int shuffle, int relabel, int64_t lo, int64_t hi, int32_t *src, int32_t *dst,
+               int nthreads)
 {
     if (scale < 1 || scale > 31 || n < 1 || n > (1ll << scale) || m < 0) return 1;
     if (a < 0 || b < 0 || c < 0 || a + b + c > 1.0) return 1;
@@ -216,30 +221,30 @@ int synth_rmat(uint64_t seed, int scale, int64_t n, int64_t m, double a, double 
     J.ta = s1 >= 1.0 ? 0xFFFFFFFFu : (uint32_t)floor(s1 * 4294967296.0);
     J.tab = s2 >= 1.0 ? 0xFFFFFFFFu : (uint32_t)floor(s2 * 4294967296.0);
     J.tabc = s3 >= 1.0 ? 0xFFFFFFFFu : (uint32_t)floor(s3 * 4294967296.0);
-    return run_parallel(&J, nthreads);
+    return run_parallel(&J, lo, hi, nthreads);
 }
 
 /* 4-neighbour side x side grid, both directions: m = 4 * side * (side - 1). */
-int synth_grid(uint64_t seed, int64_t side, int shuffle, int relabel, int32_t *src,
-               int32_t *dst, int nthreads)
+int synth_grid(uint64_t seed, int64_t side, int shuffle, int relabel, int64_t lo, int64_t hi,
+               int32_t *src, int32_t *dst, int nthreads)
 {
     if (side < 2 || side * side > 2147483647ll) return 1;
     job_t J;
     common_init(&J, seed, side * side, 4 * side * (side - 1), shuffle, relabel, src, dst);
     J.kind = KIND_GRID;
     J.side = side;
-    return run_parallel(&J, nthreads);
+    return run_parallel(&J, lo, hi, nthreads);
 }
 
 /* Erdos-Renyi style: m edges with independent uniform endpoints. */
-int synth_er(uint64_t seed, int64_t n, int64_t m, int shuffle, int relabel, int32_t *src,
-             int32_t *dst, int nthreads)
+int synth_er(uint64_t seed, int64_t n, int64_t m, int shuffle, int relabel, int64_t lo,
+             int64_t hi, int32_t *src, int32_t *dst, int nthreads)
 {
     if (n < 1 || n > 2147483647ll || m < 0) return 1;
     job_t J;
     common_init(&J, seed, n, m, shuffle, relabel, src, dst);
     J.kind = KIND_ER;
-    return run_parallel(&J, nthreads);
+    return run_parallel(&J, lo, hi, nthreads);
 }
 
 /* out[i] = the Feistel permutation of [0, N) under key(seed, stream) at i. */

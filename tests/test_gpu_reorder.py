@@ -1,0 +1,185 @@
+"""GPU parity of the BOBA reorder against the oracle, through the C ABI.
+
+perm, src_out and dst_out are integer results and must match bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def boba():
+    import paper_2306_10410_gb300 as b
+    b.load()
+    return b
+
+
+def gpu_reorder(boba, I, J, n, label=False):
+    src = torch.from_numpy(np.ascontiguousarray(I, dtype=np.int32)).cuda()
+    dst = torch.from_numpy(np.ascontiguousarray(J, dtype=np.int32)).cuda()
+    lab = torch.empty(n, dtype=torch.int32, device="cuda") if label else None
+    perm, so, do = boba.reorder(src, dst, n, label_out=lab)
+    boba.stream_status()
+    out = (perm.cpu().numpy(), so.cpu().numpy(), do.cpu().numpy())
+    return out + ((lab.cpu().numpy(),) if label else ())
+
+
+def assert_parity(boba, I, J, n):
+    perm, so, do, lab = gpu_reorder(boba, I, J, n, label=True)
+    operm, olab = oracle.boba_perm(I, J, n)
+    oso, odo = oracle.relabel(I, J, olab, n)
+    np.testing.assert_array_equal(perm, operm)
+    np.testing.assert_array_equal(lab, olab)
+    np.testing.assert_array_equal(so, oso)
+    np.testing.assert_array_equal(do, odo)
+
+
+def test_fig2_roads(boba, golden):
+    g = golden("fig2_roads.txt")
+    alphabet = sorted(set(g["I"]))
+    I = [alphabet.index(t) for t in g["I"]]
+    J = [alphabet.index(t) for t in g["J"]]
+    perm, _, _ = gpu_reorder(boba, I, J, 13)
+    assert [alphabet[v] for v in perm] == g["order"]
+
+
+def test_rmat14_config(boba):
+    """R-MAT scale 14, 262,144 edges: bit-exact perm / src_out / dst_out / label."""
+    w = synth.RMAT14
+    I, J = w.generate()
+    assert_parity(boba, I, J, w.n)
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 5, 7, 1023, 4097, 65537, 300001])
+def test_ragged_sizes(boba, m):
+    """Several tiles and a ragged tail (m not a multiple of 4 or of a tile)."""
+    n = max(2, m // 7)
+    I, J = synth.er(n, m, seed=m)
+    assert_parity(boba, I, J, n)
+
+
+@pytest.mark.parametrize("n", [1, 5, 1023, 1024, 1025, 5000, 200003])
+def test_isolated_heavy(boba, n):
+    """Far more vertices than edges: the isolated tail dominates."""
+    m = max(1, n // 50)
+    I, J = synth.er(n, m, seed=n + 1)
+    assert_parity(boba, I, J, n)
+
+
+def test_empty_graph_identity(boba):
+    n = 3000
+    I = np.zeros(0, np.int32)
+    perm, so, do = gpu_reorder(boba, I, I, n)
+    np.testing.assert_array_equal(perm, np.arange(n))
+    assert so.size == 0 and do.size == 0
+
+
+def test_self_loops_and_hub(boba):
+    n = 4096
+    rng = np.random.default_rng(1)
+    I = rng.integers(0, n, 100000).astype(np.int32)
+    J = I.copy()                                             # all self-loops
+    assert_parity(boba, I, J, n)
+    I = np.full(1 << 20, 77, np.int32)                       # one hub edge, 2^20 times
+    J = np.full(1 << 20, 3, np.int32)
+    assert_parity(boba, I, J, n)
+
+
+def test_misaligned_views(boba):
+    """Inputs that are not 16-byte aligned take the scalar path; same results."""
+    w = synth.RMAT14
+    I, J = w.generate()
+    src = torch.from_numpy(I).cuda()
+    dst = torch.from_numpy(J).cuda()
+    for off in (1, 2, 3):
+        s, d = src[off:], dst[off:]
+        perm, so, do = boba.reorder(s, d, w.n)
+        boba.stream_status()
+        operm, oso, odo = oracle.reorder(I[off:], J[off:], w.n)
+        np.testing.assert_array_equal(perm.cpu().numpy(), operm)
+        np.testing.assert_array_equal(so.cpu().numpy(), oso)
+        np.testing.assert_array_equal(do.cpu().numpy(), odo)
+
+
+def test_in_place_aliasing(boba):
+    w = synth.RMAT14
+    I, J = w.generate()
+    src = torch.from_numpy(I.copy()).cuda()
+    dst = torch.from_numpy(J.copy()).cuda()
+    perm, so, do = boba.reorder(src, dst, w.n, src_out=src, dst_out=dst)
+    boba.stream_status()
+    operm, oso, odo = oracle.reorder(I, J, w.n)
+    np.testing.assert_array_equal(src.cpu().numpy(), oso)
+    np.testing.assert_array_equal(dst.cpu().numpy(), odo)
+
+
+def test_perm_only_and_cached_workspace_entry(boba):
+    w = synth.RMAT14
+    I, J = w.generate()
+    src = torch.from_numpy(I).cuda()
+    dst = torch.from_numpy(J).cuda()
+    operm, oso, odo = oracle.reorder(I, J, w.n)
+    perm = boba.reorder_perm(src, dst, w.n)
+    boba.stream_status()
+    np.testing.assert_array_equal(perm.cpu().numpy(), operm)
+    # boba_reorder: the library-managed workspace form
+    p2 = torch.empty(w.n, dtype=torch.int32, device="cuda")
+    so = torch.empty_like(src)
+    do = torch.empty_like(dst)
+    for _ in range(2):
+        rc = boba.boba_reorder(src, dst, src.numel(), w.n, p2, so, do)
+        assert rc == 0
+        boba.stream_status()
+        np.testing.assert_array_equal(p2.cpu().numpy(), operm)
+        np.testing.assert_array_equal(so.cpu().numpy(), oso)
+
+
+def test_out_of_range_ids_reported(boba):
+    n = 100
+    I = np.array([1, 2, 150, 3], np.int32)
+    J = np.array([4, -5, 6, 7], np.int32)
+    src = torch.from_numpy(I).cuda()
+    dst = torch.from_numpy(J).cuda()
+    perm, so, do = boba.reorder(src, dst, n)
+    with pytest.raises(boba.BobaError) as e:
+        boba.stream_status()
+    assert e.value.code == 2
+    so, do = so.cpu().numpy(), do.cpu().numpy()
+    assert so[2] == -1 and do[1] == -1
+    boba.stream_status()                          # the word was cleared
+
+
+def test_bad_arguments(boba):
+    src = torch.zeros(4, dtype=torch.int32, device="cuda")
+    perm = torch.zeros(4, dtype=torch.int32, device="cuda")
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    assert boba.boba_reorder_ex(src, src, 4, 0, perm, src, src, None, ws, ws.numel()) == 1
+    assert boba.boba_reorder_ex(src, src, 4, 4, perm, src, None, None, ws, ws.numel()) == 1
+    assert boba.boba_reorder_ex(src, src, 4, 4, perm, src, src, None, ws, 16) == 4
+    assert boba.boba_reorder_ex(src, src, 1 << 31, 4, perm, src, src, None, ws, ws.numel()) == 3
+
+
+def test_idempotent_on_gpu(boba):
+    I, J = synth.rmat(16, 1 << 20, seed=77)
+    n = 1 << 16
+    perm, so, do = gpu_reorder(boba, I, J, n)
+    perm2, so2, do2 = gpu_reorder(boba, so, do, n)
+    np.testing.assert_array_equal(perm2[: len(np.unique(np.r_[I, J]))],
+                                  np.arange(len(np.unique(np.r_[I, J]))))
+    np.testing.assert_array_equal(so2, so)
+    np.testing.assert_array_equal(do2, do)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("wname", ["rmat24_m2^28", "grid4096", "er24_m2^27"])
+def test_full_size_bit_exact(boba, wname):
+    """The full-size workloads, in the launch configuration the benchmark times,
+    checked element by element against the oracle."""
+    w = synth.WORKLOADS[wname]
+    I, J = w.generate()
+    assert_parity(boba, I, J, w.n)

@@ -74,3 +74,13 @@ def test_batch_sizes_recipe():
     for g in range(6):
         ng = vo[g + 1] - vo[g]
         assert s[eo[g]:eo[g + 1]].max() < ng and d[eo[g]:eo[g + 1]].max() < ng
+
+
+def test_edge_range_is_a_slice():
+    full = synth.rmat(12, 100000, seed=10)
+    part = synth.rmat(12, 100000, seed=10, edge_range=(30000, 70001))
+    assert np.array_equal(part[0], full[0][30000:70001])
+    assert np.array_equal(part[1], full[1][30000:70001])
+    g = synth.grid(20, seed=3)
+    gp = synth.grid(20, seed=3, edge_range=(5, 17))
+    assert np.array_equal(gp[0], g[0][5:17])
