@@ -286,7 +286,8 @@ def run_ours(args):
                     "frac": round(full / (reorder_ms * 1e-3) / 1e9 / hbm, 4)}
 
     # end-to-end through the public API with host buffers
-    e2e = run_e2e(args, boba, torch, dev, stream, src_h, dst_h, m, n, world)
+    e2e = None if args.no_e2e else run_e2e(args, boba, torch, dev, stream, src_h, dst_h, m, n,
+                                           world)
 
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": "Gedges/s", "n_gpus": world,
@@ -437,6 +438,7 @@ def main():
     ap.add_argument("--spmv-iters", type=int, default=20)
     ap.add_argument("--cpu-sample-edges", type=int, default=1 << 27)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)        # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -188,8 +188,10 @@ RMAT24 = Workload("rmat24_m2^28", "rmat", 1 << 24, 1 << 28, SEED_BASE + 1, scale
 GRID4096 = Workload("grid4096", "grid", 4096 * 4096, 4 * 4096 * 4095, SEED_BASE + 2,
                     side=4096)
 ER24 = Workload("er24_m2^27", "er", 1 << 24, 1 << 27, SEED_BASE + 12)
+# A quarter-size R-MAT scale 24 (2^26 edges, 512 MiB of input > L2) for profiling captures.
+RMAT24_SMALL = Workload("rmat24_m2^26", "rmat", 1 << 24, 1 << 26, SEED_BASE + 1, scale=24)
 
-WORKLOADS = {w.name: w for w in (RMAT14, RMAT24, GRID4096, ER24)}
+WORKLOADS = {w.name: w for w in (RMAT14, RMAT24, GRID4096, ER24, RMAT24_SMALL)}
 
 
 def batch_sizes(G: int, seed: int, log2_lo: float = 8.0, log2_hi: float = 18.0,
