@@ -102,6 +102,42 @@ boba_status_t boba_reorder_ex(const int32_t *src, const int32_t *dst, int64_t m,
                               int32_t *perm_out, int32_t *src_out, int32_t *dst_out,
                               int32_t *label_out, void *ws, size_t ws_bytes, void *stream);
 
+/*
+ * boba_reorder_static -- boba_reorder for callers that cannot allocate device
+ * memory.  (The paper has no counterpart: this is a deployment variant.)
+ *
+ * Who needs it: code that runs where cudaMalloc is not available or not
+ * allowed -- inside a process whose device memory is all owned by one pool or
+ * arena, in a plug-in whose host framework forbids allocation on its hot
+ * path, or in a latency-bound loop that cannot afford the implicit device
+ * synchronisation of an allocation.  Such a caller passes only its inputs and
+ * outputs; the scratch lives in a fixed array inside the library's device
+ * image (10 MiB, held on every GPU that loads the library until the process
+ * exits).  This entry point calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *
+ * Arguments and results are those of boba_reorder (same bits), plus:
+ *   error_bits  device pointer to one uint32_t, or NULL.  Kernels OR
+ *               (1u << code) into it for device-side errors (an ID outside
+ *               [0, n): BOBA_ERR_ID_OUT_OF_RANGE; a look-back wait that gave
+ *               up: BOBA_ERR_TIMEOUT); the caller clears it.  These errors are
+ *               not reported by boba_stream_status().  With NULL they are not
+ *               reported at all; an out-of-range ID still shows as -1 in
+ *               src_out/dst_out.
+ * Limits: m <= 2^22 edges and n <= 2^20 vertices; larger graphs return
+ * BOBA_ERR_TOO_LARGE before anything is launched.
+ * The first call on a device sets up that device (it looks up the device
+ * address of the scratch array and caches launch sizes); make that first call
+ * before any stream capture.  Every call on every stream of a device shares
+ * the one scratch array, which keeps the last call's contents: calls whose
+ * kernels overlap on the GPU (different streams, or other threads) race and
+ * give wrong results, so order them on one stream or synchronise between
+ * them.  Each call re-initialises all scratch state it relies on.
+ */
+boba_status_t boba_reorder_static(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                                  int32_t *perm_out, int32_t *src_out, int32_t *dst_out,
+                                  uint32_t *error_bits, void *stream);
+
 /* ------------------------------------------------------------------------
  * Batched reordering: G independent graphs in one persistent launch
  * ------------------------------------------------------------------------ */

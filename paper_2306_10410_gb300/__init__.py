@@ -14,7 +14,7 @@ from ._lib import BobaError, STATUS_NAMES, check, load
 
 __all__ = [
     "BobaError", "load", "reorder", "reorder_perm", "coo_to_csr", "spmv", "stream_status",
-    "boba_reorder", "boba_reorder_ex", "boba_reorder_workspace_bytes", "boba_reorder_batched",
+    "boba_reorder", "boba_reorder_ex", "boba_reorder_workspace_bytes", "boba_reorder_static", "boba_reorder_batched",
     "boba_reorder_batched_workspace_bytes", "boba_coo_to_csr", "boba_coo_to_csr_workspace_bytes",
     "boba_spmv_csr", "boba_spmv_workspace_bytes", "boba_stream_status", "boba_status_string",
     "Workspace", "kernel_timing",
@@ -59,6 +59,13 @@ def boba_reorder_ex(src, dst, m, n, perm_out, src_out, dst_out, label_out, ws, w
                     stream=None):
     return load().boba_reorder_ex(_p(src), _p(dst), m, n, _p(perm_out), _p(src_out),
                                   _p(dst_out), _p(label_out), _p(ws), ws_bytes, _s(stream))
+
+
+def boba_reorder_static(src, dst, m, n, perm_out, src_out, dst_out, error_bits=None,
+                        stream=None):
+    """The allocation-free reorder (scratch in the library's static device array)."""
+    return load().boba_reorder_static(_p(src), _p(dst), m, n, _p(perm_out), _p(src_out),
+                                      _p(dst_out), _p(error_bits), _s(stream))
 
 
 def boba_reorder_batched(src, dst, edge_off, vert_off, G, max_m, max_n, total_m, total_n,

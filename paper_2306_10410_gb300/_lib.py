@@ -33,6 +33,7 @@ SIGNATURES = {
     "boba_reorder": (_ST, [_P, _P, _I64, _I64, _P, _P, _P, _P]),
     "boba_reorder_workspace_bytes": (_SZ, [_I64, _I64]),
     "boba_reorder_ex": (_ST, [_P, _P, _I64, _I64, _P, _P, _P, _P, _P, _SZ, _P]),
+    "boba_reorder_static": (_ST, [_P, _P, _I64, _I64, _P, _P, _P, _P, _P]),
     "boba_reorder_batched": (_ST, [_P, _P, _P, _P, _I64, _I64, _I64, _I64, _I64, _P, _P, _P,
                                    _P, _SZ, _P]),
     "boba_reorder_batched_workspace_bytes": (_SZ, [_I64, _I64, _I64]),

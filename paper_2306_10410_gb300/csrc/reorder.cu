@@ -284,6 +284,17 @@ __global__ void __launch_bounds__(kRelabelBlock) k_relabel(const int32_t *src, c
     }
 }
 
+template __global__ void k_first<true>(const int32_t *__restrict__, const int32_t *__restrict__,
+                                       int64_t, uint32_t, uint32_t *, uint32_t *);
+template __global__ void k_first<false>(const int32_t *__restrict__, const int32_t *__restrict__,
+                                        int64_t, uint32_t, uint32_t *, uint32_t *);
+template __global__ void k_relabel<true>(const int32_t *, const int32_t *, int64_t, uint32_t,
+                                         const int32_t *__restrict__, int32_t *, int32_t *,
+                                         uint32_t *);
+template __global__ void k_relabel<false>(const int32_t *, const int32_t *, int64_t, uint32_t,
+                                          const int32_t *__restrict__, int32_t *, int32_t *,
+                                          uint32_t *);
+
 boba_status_t launch_reorder(const ReorderArgs &a, int64_t n4, size_t nzero_u32,
                              cudaStream_t stream)
 {
@@ -335,38 +346,6 @@ boba_status_t launch_reorder(const ReorderArgs &a, int64_t n4, size_t nzero_u32,
     }
     BOBA_LAUNCH_CHECK();
     return BOBA_OK;
-}
-
-}  // namespace boba
-
-namespace boba {
-
-struct ReorderLayout {
-    int64_t n4, nwords, ngroups, scan_tiles, emit_tiles;
-    size_t key, label, grp, zero_begin, bitmap, tstat_scan, tstat_emit, counters, zero_end, total;
-};
-
-static bool reorder_layout(int64_t m, int64_t n, ReorderLayout &L)
-{
-    if (m < 0 || n < 0 || m > kMaxSize || n > kMaxSize) return false;
-    L.n4 = align_up((size_t)(n > 0 ? n : 1), 4);
-    L.nwords = (int64_t)align_up((size_t)cdiv(2 * m, 32) > 0 ? (size_t)cdiv(2 * m, 32) : 1,
-                                 kScanTileWords);
-    L.ngroups = L.nwords / 8;
-    L.scan_tiles = L.nwords / kScanTileWords;
-    L.emit_tiles = cdiv(n > 0 ? n : 1, kEmitTileVerts);
-    Carve c;
-    L.key = c.take(L.n4 * 4);
-    L.label = c.take(L.n4 * 4);
-    L.grp = c.take(L.ngroups * 4);
-    L.zero_begin = c.off;
-    L.bitmap = c.take(L.nwords * 4);
-    L.tstat_scan = c.take(L.scan_tiles * 8);
-    L.tstat_emit = c.take(L.emit_tiles * 8);
-    L.counters = c.take(kNumCounters * 4);
-    L.zero_end = c.off;
-    L.total = c.off;
-    return true;
 }
 
 }  // namespace boba

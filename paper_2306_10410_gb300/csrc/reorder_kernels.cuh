@@ -3,6 +3,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "host.hpp"
 
 namespace boba {
 
@@ -68,7 +69,54 @@ __device__ __forceinline__ int32_t comp(const int4 &q, int j)
     return j == 0 ? q.x : j == 1 ? q.y : j == 2 ? q.z : q.w;
 }
 
+// Workspace layout of one reorder (byte offsets from a 256-byte-aligned base).
+struct ReorderLayout {
+    int64_t n4, nwords, ngroups, scan_tiles, emit_tiles;
+    size_t key, label, grp, zero_begin, bitmap, tstat_scan, tstat_emit, counters, zero_end, total;
+};
+
+inline bool reorder_layout(int64_t m, int64_t n, ReorderLayout &L)
+{
+    if (m < 0 || n < 0 || m > kMaxSize || n > kMaxSize) return false;
+    L.n4 = align_up((size_t)(n > 0 ? n : 1), 4);
+    L.nwords = (int64_t)align_up((size_t)cdiv(2 * m, 32) > 0 ? (size_t)cdiv(2 * m, 32) : 1,
+                                 kScanTileWords);
+    L.ngroups = L.nwords / 8;
+    L.scan_tiles = L.nwords / kScanTileWords;
+    L.emit_tiles = cdiv(n > 0 ? n : 1, kEmitTileVerts);
+    Carve c;
+    L.key = c.take(L.n4 * 4);
+    L.label = c.take(L.n4 * 4);
+    L.grp = c.take(L.ngroups * 4);
+    L.zero_begin = c.off;
+    L.bitmap = c.take(L.nwords * 4);
+    L.tstat_scan = c.take(L.scan_tiles * 8);
+    L.tstat_emit = c.take(L.emit_tiles * 8);
+    L.counters = c.take(kNumCounters * 4);
+    L.zero_end = c.off;
+    L.total = c.off;
+    return true;
+}
+
 boba_status_t launch_reorder(const ReorderArgs &a, int64_t n4, size_t nzero_u32,
                              cudaStream_t stream);
+
+// The kernels of the pipeline (defined in reorder.cu).
+__global__ void k_init(uint32_t *__restrict__ key, int64_t n4, uint32_t *__restrict__ zero,
+                       int64_t nzero);
+template <bool VEC>
+__global__ void k_first(const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                        int64_t m, uint32_t n, uint32_t *key, uint32_t *status);
+__global__ void k_mark(const uint32_t *__restrict__ key, int64_t n4, uint32_t *bitmap);
+__global__ void k_scan(const uint32_t *__restrict__ bitmap, uint32_t *__restrict__ grp,
+                       uint64_t *tstat, uint32_t *counters, int64_t tiles, uint32_t *status);
+__global__ void k_emit(const uint32_t *__restrict__ key, uint32_t n,
+                       const uint32_t *__restrict__ bitmap, const uint32_t *__restrict__ grp,
+                       int32_t *__restrict__ label, int32_t *__restrict__ perm, uint64_t *tstat,
+                       uint32_t *counters, bool label_vec, uint32_t *status);
+template <bool VEC>
+__global__ void k_relabel(const int32_t *src, const int32_t *dst, int64_t m, uint32_t n,
+                          const int32_t *__restrict__ label, int32_t *src_out, int32_t *dst_out,
+                          uint32_t *status);
 
 }  // namespace boba
