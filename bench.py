@@ -281,6 +281,11 @@ def run_ours(args):
         roof = {"kernel": dom, "bound": "hbm", "achieved": kern[dom]["achieved_gbs"],
                 "peak": hbm, "unit": "GB/s", "frac": kern[dom]["frac"], "traffic": traffic,
                 "peak_source": peak_kind}
+    # SpMV and CSR on the BOBA order vs the random (input) order, same kernels
+    compare = None
+    if have_csr:
+        compare = compare_orders(args, boba, torch, dev, stream, src, dst, so, do, m, n,
+                                 row_ptr, col, val, ws_c, ws_s, x, y, flush)
     full = 24 * m + 4 * n
     reorder_roof = {"alg_bytes": full, "achieved_gbs": round(full / (reorder_ms * 1e-3) / 1e9, 1),
                     "frac": round(full / (reorder_ms * 1e-3) / 1e9 / hbm, 4)}
@@ -302,6 +307,7 @@ def run_ours(args):
                       "csr": round(statistics.mean(t_csr), 4) if t_csr else None,
                       "spmv_total": round(statistics.mean(t_spmv), 4) if t_spmv else None},
         "reorder_roofline": reorder_roof,
+        "orders": compare,
         "roofline": roof,
         "kernels": kern,
         "gpu_launches": launches,
@@ -315,6 +321,38 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def compare_orders(args, boba, torch, dev, stream, src, dst, so, do, m, n, row_ptr, col, val,
+                   ws_c, ws_s, x, y, flush):
+    """CSR build and SpMV GB/s on the random input order vs the BOBA order (Sec. 5.6)."""
+    out = {}
+    spmv_bytes = 8 * m + 16 * n
+    for name, (s_, d_) in (("random", (src, dst)), ("boba", (so, do))):
+        t_csr, t_spmv = [], []
+        for rep in range(max(3, min(args.steps, 5)) + 1):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(stream)
+            boba.check(boba.boba_coo_to_csr(s_, d_, m, n, row_ptr, col, val, ws_c, ws_c.numel(),
+                                            stream), "csr")
+            ev[1].record(stream)
+            for _ in range(args.spmv_iters):
+                boba.check(boba.boba_spmv_csr(row_ptr, col, val, x, y, n, m, ws_s, ws_s.numel(),
+                                              stream), "spmv")
+            ev[2].record(stream)
+            torch.cuda.synchronize(dev)
+            if rep:                                  # first repetition is warm-up
+                t_csr.append(ev[0].elapsed_time(ev[1]))
+                t_spmv.append(ev[1].elapsed_time(ev[2]) / max(1, args.spmv_iters))
+        boba.stream_status(stream)
+        ms = statistics.median(t_spmv)
+        out[name] = {"csr_ms": round(statistics.median(t_csr), 4), "spmv_ms": round(ms, 4),
+                     "spmv_gbs": round(spmv_bytes / (ms * 1e-3) / 1e9, 1)}
+    out["spmv_speedup_boba_vs_random"] = round(out["random"]["spmv_ms"] / out["boba"]["spmv_ms"], 3)
+    out["csr_speedup_boba_vs_random"] = round(out["random"]["csr_ms"] / out["boba"]["csr_ms"], 3)
+    out["spmv_bytes_per_launch"] = spmv_bytes
+    return out
 
 
 def run_e2e(args, boba, torch, dev, stream, src_h, dst_h, m, n, world):

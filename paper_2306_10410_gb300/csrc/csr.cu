@@ -1,0 +1,349 @@
+// COO -> CSR for the pull SpMV of Alg. 3 (arXiv 2306.10410, Sec. 1.2.2):
+// rows are destinations, columns are sources, entries of a row keep the input
+// edge order, and the entry of edge u -> v holds fp32(1 / outdeg(u)).
+//
+// A stable LSD radix sort of (key = dst, value = src) with 8-bit digits:
+//   k_csr_hist      per-digit histograms of all passes in one read of dst, and
+//                   outdeg(u) by atomic increments over src
+//   k_csr_digits    exclusive scan of each pass's 256 digit counts
+//   k_csr_pass      one pass: stable in-tile ranking (warp match + per-warp
+//                   digit counters, items striped so processing order is input
+//                   order), per-digit decoupled look-back across tiles, and a
+//                   scatter staged through shared memory so that runs of equal
+//                   digits are written contiguously (Adinets and Merrill,
+//                   "Onesweep", 2022, for the single-pass scheme)
+//   k_csr_finish    row_ptr from the boundaries of the sorted keys and
+//                   val = fp32(1 / outdeg(col))
+#include "common.cuh"
+#include "host.hpp"
+
+namespace boba {
+namespace {
+
+constexpr int kPassBlock = 256;
+constexpr int kPassItems = 16;                       // per thread
+constexpr int kPassTile = kPassBlock * kPassItems;  // 4096 items
+constexpr int kWarps = kPassBlock / 32;
+constexpr int kMaxPasses = 4;                        // 32-bit keys
+constexpr int kNumCtr = 16;
+
+// Look-back status of (tile, digit) for pass p, one u64: the top 4 bits hold
+// 2p+1 (aggregate) or 2p+2 (inclusive prefix); anything else (0, or an earlier
+// pass's flags) is "not ready".  One array serves all passes of a call.
+__device__ __forceinline__ uint64_t pass_flag(int p, bool inclusive)
+{
+    return (uint64_t)(2 * p + (inclusive ? 2 : 1)) << 60;
+}
+constexpr uint64_t kPassValMask = (1ull << 60) - 1;
+
+struct CsrLayout {
+    int passes;
+    int64_t tiles;
+    size_t kA, vA, kB, vB, outdeg, hist, dstart, status, counters, total, zero_begin, zero_end;
+};
+
+bool csr_layout(int64_t m, int64_t n, CsrLayout &L)
+{
+    if (m < 0 || n < 0 || m > kMaxSize || n > kMaxSize) return false;
+    int bits = 1;
+    while (bits < 31 && (1ll << bits) < n) bits++;
+    L.passes = (bits + 7) / 8;
+    L.tiles = cdiv(m > 0 ? m : 1, kPassTile);
+    const size_t mm = (size_t)(m > 0 ? m : 1);
+    Carve c;
+    L.kA = c.take(mm * 4);
+    L.vA = c.take(mm * 4);
+    L.kB = c.take(mm * 4);
+    L.vB = c.take(mm * 4);
+    L.zero_begin = c.off;
+    L.outdeg = c.take((size_t)(n > 0 ? n : 1) * 4);
+    L.hist = c.take(kMaxPasses * 256 * 4);
+    L.status = c.take((size_t)L.tiles * 256 * 8);
+    L.counters = c.take(kNumCtr * 4);
+    L.zero_end = c.off;
+    L.dstart = c.take(kMaxPasses * 256 * 4);
+    L.total = c.off;
+    return true;
+}
+
+__global__ void __launch_bounds__(256) k_zero(uint4 *p, int64_t n16)
+{
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = z;
+}
+
+// Digit histograms of every pass over dst, plus outdeg over src.
+__global__ void __launch_bounds__(256) k_csr_hist(const int32_t *__restrict__ src,
+                                                  const int32_t *__restrict__ dst, int64_t m,
+                                                  uint32_t n, int passes, uint32_t *outdeg,
+                                                  uint32_t *hist, uint32_t *status)
+{
+    __shared__ uint32_t sh[kMaxPasses * 256];
+    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+        const uint32_t k = (uint32_t)ld_stream(dst + e);
+        const uint32_t s = (uint32_t)ld_stream(src + e);
+        for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * 256 + ((k >> (8 * p)) & 255u)], 1u);
+        if (s < n) atomicAdd(&outdeg[s], 1u);
+        else raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE);
+        if (k >= n) raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// dstart[p][d] = exclusive prefix of hist[p][.] (one block of 256 threads).
+__global__ void __launch_bounds__(256) k_csr_digits(const uint32_t *__restrict__ hist,
+                                                    uint32_t *__restrict__ dstart, int passes)
+{
+    __shared__ typename BlockScan<256>::Smem sm;
+    for (int p = 0; p < passes; ++p) {
+        uint32_t tot;
+        const uint32_t ex = BlockScan<256>::exclusive(hist[p * 256 + threadIdx.x], &tot, sm);
+        dstart[p * 256 + threadIdx.x] = ex;
+        __syncthreads();
+    }
+}
+
+// One stable LSD pass over digit p (bits 8p .. 8p+7).
+__global__ void __launch_bounds__(kPassBlock) k_csr_pass(
+    const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
+    uint32_t *__restrict__ vout, int64_t m, int p, const uint32_t *__restrict__ dstart,
+    uint64_t *status_lb, uint32_t *counters, uint32_t *status)
+{
+    __shared__ uint32_t s_keys[kPassTile];
+    __shared__ uint32_t s_vals[kPassTile];
+    __shared__ uint16_t s_wcnt[kWarps][256];      // per-warp digit counts, then warp prefixes
+    __shared__ uint32_t s_tpre[256];               // tile-local exclusive digit offsets
+    __shared__ uint32_t s_base[256];               // global start of this tile's run of digit d
+    __shared__ typename BlockScan<256>::Smem sm;
+    __shared__ uint32_t s_tile;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&counters[p], 1u);
+    for (int i = threadIdx.x; i < kWarps * 256; i += kPassBlock) (&s_wcnt[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t t0 = tile * kPassTile;
+    const int shift = 8 * p;
+
+    // load: item (warp, k, lane) is tile index warp*512 + k*32 + lane, so the
+    // k-major / lane-minor processing order of a warp is the input order
+    uint32_t key[kPassItems], val[kPassItems], rank[kPassItems];
+#pragma unroll
+    for (int k = 0; k < kPassItems; ++k) {
+        const int64_t i = t0 + warp * (32 * kPassItems) + k * 32 + lane;
+        if (i < m) {
+            key[k] = __ldcs(kin + i);
+            val[k] = __ldcs(vin + i);
+        } else {
+            key[k] = 0xFFFFFFFFu;
+            val[k] = 0;
+        }
+    }
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int k = 0; k < kPassItems; ++k) {
+        const int64_t i = t0 + warp * (32 * kPassItems) + k * 32 + lane;
+        const bool valid = i < m;
+        const uint32_t d = valid ? ((key[k] >> shift) & 255u) : 256u;
+        const unsigned peers = __match_any_sync(kFull, d);
+        const int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (valid && lane == leader) {
+            old = s_wcnt[warp][d];
+            s_wcnt[warp][d] = (uint16_t)(old + __popc(peers));
+        }
+        old = __shfl_sync(kFull, old, leader);
+        rank[k] = old + __popc(peers & lt);
+        __syncwarp();
+    }
+    __syncthreads();
+    // digit d = threadIdx.x: tile count, warp prefixes, tile-local offsets
+    const int d = threadIdx.x;
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        const uint32_t c = s_wcnt[w][d];
+        s_wcnt[w][d] = (uint16_t)cnt;
+        cnt += c;
+    }
+    uint32_t tot;
+    const uint32_t tpre = BlockScan<256>::exclusive(cnt, &tot, sm);
+    s_tpre[d] = tpre;
+
+    // per-digit look-back across tiles (thread d owns digit d)
+    {
+        uint64_t *st = status_lb + tile * 256 + d;
+        if (tile == 0) {
+            st_relaxed_u64(st, pass_flag(p, true) | cnt);
+            s_base[d] = dstart[p * 256 + d];
+        } else {
+            st_relaxed_u64(st, pass_flag(p, false) | cnt);
+            uint64_t excl = 0;
+            int64_t t = tile - 1;
+            uint64_t tstart = 0;
+            uint32_t spins = 0;
+            while (t >= 0) {
+                const uint64_t s = ld_relaxed_u64(status_lb + t * 256 + d);
+                const uint64_t f = s & ~kPassValMask;
+                if (f == pass_flag(p, true)) { excl += s & kPassValMask; break; }
+                if (f == pass_flag(p, false)) { excl += s & kPassValMask; --t; continue; }
+                if ((++spins & 255u) == 1u) {
+                    const uint64_t now = globaltimer_ns();
+                    if (tstart == 0) tstart = now;
+                    else if (now - tstart > kTimeoutNs) {
+                        raise_status(status, BOBA_ERR_TIMEOUT);
+                        break;
+                    }
+                }
+                __nanosleep(32);
+            }
+            st_relaxed_u64(st, pass_flag(p, true) | ((excl + cnt) & kPassValMask));
+            s_base[d] = dstart[p * 256 + d] + (uint32_t)excl;
+        }
+    }
+    __syncthreads();
+    // stage the tile in shared memory in sorted order
+#pragma unroll
+    for (int k = 0; k < kPassItems; ++k) {
+        const int64_t i = t0 + warp * (32 * kPassItems) + k * 32 + lane;
+        if (i < m) {
+            const uint32_t dd = (key[k] >> shift) & 255u;
+            const uint32_t pos = s_tpre[dd] + s_wcnt[warp][dd] + rank[k];
+            s_keys[pos] = key[k];
+            s_vals[pos] = val[k];
+        }
+    }
+    __syncthreads();
+    // write out: consecutive threads write consecutive slots of a digit run
+    const int64_t valid_n = (m - t0) < kPassTile ? (m - t0) : kPassTile;
+#pragma unroll
+    for (int k = 0; k < kPassItems; ++k) {
+        const int j = k * kPassBlock + threadIdx.x;
+        if (j < valid_n) {
+            const uint32_t kk = s_keys[j];
+            const uint32_t dd = (kk >> shift) & 255u;
+            const int64_t g = (int64_t)s_base[dd] + (j - (int64_t)s_tpre[dd]);
+            __stcs(kout + g, kk);
+            __stcs(vout + g, s_vals[j]);
+        }
+    }
+}
+
+// row_ptr[v] = number of sorted keys < v; val[i] = fp32(1 / outdeg(col[i])).
+__global__ void __launch_bounds__(256) k_csr_finish(const uint32_t *__restrict__ skeys,
+                                                    const int32_t *__restrict__ col, int64_t m,
+                                                    int64_t n, const uint32_t *__restrict__ outdeg,
+                                                    int64_t *__restrict__ row_ptr,
+                                                    float *__restrict__ val)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        const int64_t k = skeys[i] < (uint32_t)n ? (int64_t)skeys[i] : n;
+        const int64_t prev = i == 0 ? -1 : (skeys[i - 1] < (uint32_t)n ? (int64_t)skeys[i - 1] : n);
+        for (int64_t v = prev + 1; v <= k && v <= n; ++v) row_ptr[v] = i;
+        if (i == m - 1)
+            for (int64_t v = k + 1; v <= n; ++v) row_ptr[v] = m;
+        const uint32_t c = (uint32_t)col[i];
+        const uint32_t dg = c < (uint32_t)n ? __ldg(outdeg + c) : 0u;
+        float r;
+        if (dg == 0) r = 0.0f;
+        else if (dg < (1u << 24)) r = __frcp_rn((float)dg);      // exact operand, IEEE rounding
+        else r = (float)(1.0 / (double)dg);
+        __stcs(val + i, r);
+    }
+}
+
+__global__ void k_rowptr_zero(int64_t *row_ptr, int64_t n)
+{
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v <= n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        row_ptr[v] = 0;
+}
+
+}  // namespace
+}  // namespace boba
+
+using namespace boba;
+
+extern "C" size_t boba_coo_to_csr_workspace_bytes(int64_t m, int64_t n)
+{
+    CsrLayout L;
+    if (!csr_layout(m, n, L)) return 0;
+    return L.total;
+}
+
+extern "C" boba_status_t boba_coo_to_csr(const int32_t *src, const int32_t *dst, int64_t m,
+                                         int64_t n, int64_t *row_ptr, int32_t *col_out,
+                                         float *val_out, void *ws, size_t ws_bytes, void *stream_)
+{
+    if (m < 0 || n < 0) return BOBA_ERR_INVALID_ARG;
+    if (m > kMaxSize || n > kMaxSize) return BOBA_ERR_TOO_LARGE;
+    if (n == 0 && m > 0) return BOBA_ERR_INVALID_ARG;
+    if (row_ptr == nullptr) return BOBA_ERR_INVALID_ARG;
+    if (m > 0 && (src == nullptr || dst == nullptr || col_out == nullptr || val_out == nullptr))
+        return BOBA_ERR_INVALID_ARG;
+    CsrLayout L;
+    csr_layout(m, n, L);
+    if (ws == nullptr || ws_bytes < L.total || !aligned256(ws)) return BOBA_ERR_WORKSPACE;
+    const DeviceInfo *dev = device_info();
+    if (!dev) return BOBA_ERR_CUDA;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (m == 0) {
+        BOBA_TIMED("csr.finish", stream,
+                   k_rowptr_zero<<<(unsigned)cdiv(n + 1, 256) < 1024 ? (unsigned)cdiv(n + 1, 256) : 1024u,
+                                   256, 0, stream>>>(row_ptr, n));
+        BOBA_LAUNCH_CHECK();
+        return BOBA_OK;
+    }
+    char *b = static_cast<char *>(ws);
+    uint32_t *kA = reinterpret_cast<uint32_t *>(b + L.kA), *vA = reinterpret_cast<uint32_t *>(b + L.vA);
+    uint32_t *kB = reinterpret_cast<uint32_t *>(b + L.kB), *vB = reinterpret_cast<uint32_t *>(b + L.vB);
+    uint32_t *outdeg = reinterpret_cast<uint32_t *>(b + L.outdeg);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(b + L.hist);
+    uint32_t *dstart = reinterpret_cast<uint32_t *>(b + L.dstart);
+    uint64_t *lb = reinterpret_cast<uint64_t *>(b + L.status);
+    uint32_t *ctr = reinterpret_cast<uint32_t *>(b + L.counters);
+    const uint32_t nn = (uint32_t)n;
+
+    {
+        const int64_t n16 = (int64_t)(L.zero_end - L.zero_begin) / 16;
+        const int g = persistent_grid((const void *)k_zero, 256, cdiv(n16, 256));
+        BOBA_TIMED("csr.zero", stream,
+                   k_zero<<<g, 256, 0, stream>>>(reinterpret_cast<uint4 *>(b + L.zero_begin), n16));
+    }
+    {
+        const int g = persistent_grid((const void *)k_csr_hist, 256, cdiv(m, 256));
+        BOBA_TIMED("csr.hist", stream,
+                   k_csr_hist<<<g, 256, 0, stream>>>(src, dst, m, nn, L.passes, outdeg, hist,
+                                                     dev->status));
+    }
+    BOBA_TIMED("csr.digits", stream,
+               k_csr_digits<<<1, 256, 0, stream>>>(hist, dstart, L.passes));
+    const uint32_t *kin = reinterpret_cast<const uint32_t *>(dst);
+    const uint32_t *vin = reinterpret_cast<const uint32_t *>(src);
+    for (int p = 0; p < L.passes; ++p) {
+        const bool last = p == L.passes - 1;
+        uint32_t *ko = (p & 1) ? kB : kA;
+        uint32_t *vo = last ? reinterpret_cast<uint32_t *>(col_out) : ((p & 1) ? vB : vA);
+        BOBA_TIMED("csr.pass", stream,
+                   k_csr_pass<<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
+                       kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status));
+        kin = ko;
+        vin = vo;
+    }
+    {
+        const int g = persistent_grid((const void *)k_csr_finish, 256, cdiv(m, 256));
+        BOBA_TIMED("csr.finish", stream,
+                   k_csr_finish<<<g, 256, 0, stream>>>(kin, col_out, m, n, outdeg, row_ptr,
+                                                       val_out));
+    }
+    BOBA_LAUNCH_CHECK();
+    return BOBA_OK;
+}

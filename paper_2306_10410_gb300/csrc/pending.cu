@@ -9,16 +9,3 @@ extern "C" boba_status_t boba_reorder_batched(const int32_t *, const int32_t *, 
     return BOBA_ERR_INVALID_ARG;
 }
 extern "C" size_t boba_reorder_batched_workspace_bytes(int64_t, int64_t, int64_t) { return 0; }
-extern "C" boba_status_t boba_coo_to_csr(const int32_t *, const int32_t *, int64_t, int64_t,
-                                         int64_t *, int32_t *, float *, void *, size_t, void *)
-{
-    return BOBA_ERR_INVALID_ARG;
-}
-extern "C" size_t boba_coo_to_csr_workspace_bytes(int64_t, int64_t) { return 0; }
-extern "C" boba_status_t boba_spmv_csr(const int64_t *, const int32_t *, const float *,
-                                       const float *, float *, int64_t, int64_t, void *, size_t,
-                                       void *)
-{
-    return BOBA_ERR_INVALID_ARG;
-}
-extern "C" size_t boba_spmv_workspace_bytes(int64_t, int64_t) { return 0; }

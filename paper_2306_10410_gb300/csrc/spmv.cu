@@ -1,0 +1,229 @@
+// Pull SpMV, Alg. 3 (arXiv 2306.10410, Sec. 1.2.2): y(v) = sum over the
+// entries of row v of A(v,u) * x(u), fp32 products and fp32 accumulation.
+//
+//   k_spmv_rows    groups of LPR lanes per row (LPR = 32 is warp-per-row; for a
+//                  short average row length several rows share a warp).  Lane j
+//                  of a group sums entries j, j+LPR, ... with FMA; the group then
+//                  reduces with a fixed xor tree.  Rows longer than kLongRow are
+//                  set aside in a list.
+//   k_spmv_plan    one block: chunk offsets of the long rows (kChunk entries each)
+//   k_spmv_chunks  one 1024-thread block per chunk: strided FMA sums and a
+//                  fixed-order block reduction into partial[chunk]
+//   k_spmv_gather  y[long row] = its chunk partials summed in chunk order
+// Every summation order depends only on the row's position and length, so the
+// result is the same on every run, and rows of equal content give equal bits
+// whatever their index.
+#include "common.cuh"
+#include "host.hpp"
+
+namespace boba {
+namespace {
+
+constexpr int64_t kLongRow = 4096;     // entries; longer rows are chunked
+constexpr int64_t kChunk = 16384;      // entries per chunk of a long row
+constexpr int kChunkBlock = 1024;
+constexpr int kRowsBlock = 256;
+
+struct SpmvLayout {
+    int64_t cap, max_chunks;
+    size_t count, list, cstart, partial, total;
+};
+
+bool spmv_layout(int64_t n_rows, int64_t nnz, SpmvLayout &L)
+{
+    if (n_rows < 0 || nnz < 0 || n_rows > kMaxSize || nnz > kMaxSize) return false;
+    L.cap = nnz / kLongRow + 1;
+    L.max_chunks = nnz / kChunk + L.cap + 1;
+    Carve c;
+    L.count = c.take(64);
+    L.list = c.take((size_t)L.cap * 4);
+    L.cstart = c.take((size_t)(L.cap + 1) * 4);
+    L.partial = c.take((size_t)L.max_chunks * 4);
+    L.total = c.off;
+    return true;
+}
+
+template <int LPR>
+__global__ void __launch_bounds__(kRowsBlock) k_spmv_rows(
+    const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+    const float *__restrict__ val, const float *__restrict__ x, float *__restrict__ y,
+    int64_t n_rows, uint32_t *long_count, uint32_t *long_list, uint32_t cap, uint32_t *status)
+{
+    constexpr int RPW = 32 / LPR;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane % LPR;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t rb = warp * RPW; rb < n_rows; rb += nwarps * RPW) {
+        const int64_t r = rb + lane / LPR;
+        int64_t beg = 0, end = 0;
+        if (r < n_rows) {
+            beg = __ldg(row_ptr + r);
+            end = __ldg(row_ptr + r + 1);
+        }
+        const bool is_long = end - beg > kLongRow;
+        float acc = 0.0f;
+        if (!is_long) {
+#pragma unroll 4
+            for (int64_t p = beg + gl; p < end; p += LPR)
+                acc = fmaf(__ldcs(val + p), __ldg(x + __ldcs(col + p)), acc);
+        }
+#pragma unroll
+        for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if (gl == 0 && r < n_rows) {
+            if (!is_long) {
+                y[r] = acc;
+            } else {
+                const uint32_t i = atomicAdd(long_count, 1u);
+                if (i < cap) long_list[i] = (uint32_t)r;
+                else raise_status(status, BOBA_ERR_INVALID_ARG);   // row_ptr inconsistent with nnz
+            }
+        }
+    }
+}
+
+// Chunk offsets of the long rows: cstart[i] = sum over j < i of ceil(len_j / kChunk).
+__global__ void __launch_bounds__(256) k_spmv_plan(const int64_t *__restrict__ row_ptr,
+                                                   const uint32_t *long_count,
+                                                   const uint32_t *__restrict__ long_list,
+                                                   uint32_t cap, uint32_t *cstart)
+{
+    __shared__ typename BlockScan<256>::Smem sm;
+    const uint32_t L = min(*long_count, cap);
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < L; base += 256) {
+        const uint32_t i = base + threadIdx.x;
+        uint32_t c = 0;
+        if (i < L) {
+            const uint32_t r = long_list[i];
+            c = (uint32_t)cdiv(row_ptr[r + 1] - row_ptr[r], kChunk);
+        }
+        uint32_t tot;
+        const uint32_t ex = BlockScan<256>::exclusive(c, &tot, sm);
+        if (i < L) cstart[i] = carry + ex;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) cstart[L] = carry;
+}
+
+__global__ void __launch_bounds__(kChunkBlock) k_spmv_chunks(
+    const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+    const float *__restrict__ val, const float *__restrict__ x, const uint32_t *long_count,
+    const uint32_t *__restrict__ long_list, uint32_t cap, const uint32_t *__restrict__ cstart,
+    float *__restrict__ partial)
+{
+    __shared__ float s_w[kChunkBlock / 32];
+    const uint32_t L = min(*long_count, cap);
+    const uint32_t C = cstart[L];
+    for (uint32_t c = blockIdx.x; c < C; c += gridDim.x) {
+        // the long row owning chunk c: last i with cstart[i] <= c
+        uint32_t lo = 0, hi = L;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (cstart[mid] <= c) lo = mid; else hi = mid;
+        }
+        const uint32_t r = long_list[lo];
+        const int64_t beg = row_ptr[r] + (int64_t)(c - cstart[lo]) * kChunk;
+        const int64_t end = min(row_ptr[r + 1], beg + kChunk);
+        float acc = 0.0f;
+#pragma unroll 4
+        for (int64_t p = beg + threadIdx.x; p < end; p += kChunkBlock)
+            acc = fmaf(__ldcs(val + p), __ldg(x + __ldcs(col + p)), acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            float w = s_w[threadIdx.x];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(kFull, w, o);
+            if (threadIdx.x == 0) partial[c] = w;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_spmv_gather(const uint32_t *long_count,
+                                                     const uint32_t *__restrict__ long_list,
+                                                     uint32_t cap, const uint32_t *__restrict__ cstart,
+                                                     const float *__restrict__ partial,
+                                                     float *__restrict__ y)
+{
+    const uint32_t L = min(*long_count, cap);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < L; i += gridDim.x * blockDim.x) {
+        float s = 0.0f;
+        for (uint32_t c = cstart[i]; c < cstart[i + 1]; ++c) s += partial[c];
+        y[long_list[i]] = s;
+    }
+}
+
+template <int LPR>
+void launch_rows(const int64_t *row_ptr, const int32_t *col, const float *val, const float *x,
+                 float *y, int64_t n_rows, uint32_t *cnt, uint32_t *list, uint32_t cap,
+                 uint32_t *status, cudaStream_t stream)
+{
+    constexpr int RPW = 32 / LPR;
+    const int64_t warps = cdiv(n_rows, RPW);
+    const int g = persistent_grid((const void *)k_spmv_rows<LPR>, kRowsBlock,
+                                  cdiv(warps, kRowsBlock / 32));
+    BOBA_TIMED("spmv", stream,
+               k_spmv_rows<LPR><<<g, kRowsBlock, 0, stream>>>(row_ptr, col, val, x, y, n_rows, cnt,
+                                                             list, cap, status));
+}
+
+}  // namespace
+}  // namespace boba
+
+using namespace boba;
+
+extern "C" size_t boba_spmv_workspace_bytes(int64_t n_rows, int64_t nnz)
+{
+    SpmvLayout L;
+    if (!spmv_layout(n_rows, nnz, L)) return 0;
+    return L.total;
+}
+
+extern "C" boba_status_t boba_spmv_csr(const int64_t *row_ptr, const int32_t *col,
+                                       const float *val, const float *x, float *y, int64_t n_rows,
+                                       int64_t nnz, void *ws, size_t ws_bytes, void *stream_)
+{
+    if (n_rows < 0 || nnz < 0) return BOBA_ERR_INVALID_ARG;
+    if (n_rows > kMaxSize || nnz > kMaxSize) return BOBA_ERR_TOO_LARGE;
+    if (n_rows == 0) return BOBA_OK;
+    if (row_ptr == nullptr || y == nullptr || x == nullptr) return BOBA_ERR_INVALID_ARG;
+    if (nnz > 0 && (col == nullptr || val == nullptr)) return BOBA_ERR_INVALID_ARG;
+    if (x == y) return BOBA_ERR_INVALID_ARG;
+    SpmvLayout L;
+    spmv_layout(n_rows, nnz, L);
+    if (ws == nullptr || ws_bytes < L.total || !aligned256(ws)) return BOBA_ERR_WORKSPACE;
+    const DeviceInfo *dev = device_info();
+    if (!dev) return BOBA_ERR_CUDA;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    char *b = static_cast<char *>(ws);
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(b + L.count);
+    uint32_t *list = reinterpret_cast<uint32_t *>(b + L.list);
+    uint32_t *cstart = reinterpret_cast<uint32_t *>(b + L.cstart);
+    float *partial = reinterpret_cast<float *>(b + L.partial);
+    const uint32_t cap = (uint32_t)L.cap;
+
+    BOBA_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t), stream));
+    const double avg = (double)nnz / (double)n_rows;
+    if (avg <= 6.0) launch_rows<4>(row_ptr, col, val, x, y, n_rows, cnt, list, cap, dev->status, stream);
+    else if (avg <= 12.0) launch_rows<8>(row_ptr, col, val, x, y, n_rows, cnt, list, cap, dev->status, stream);
+    else if (avg <= 24.0) launch_rows<16>(row_ptr, col, val, x, y, n_rows, cnt, list, cap, dev->status, stream);
+    else launch_rows<32>(row_ptr, col, val, x, y, n_rows, cnt, list, cap, dev->status, stream);
+    if (nnz > kLongRow) {
+        BOBA_TIMED("spmv.long", stream,
+                   k_spmv_plan<<<1, 256, 0, stream>>>(row_ptr, cnt, list, cap, cstart));
+        const int g = persistent_grid((const void *)k_spmv_chunks, kChunkBlock,
+                                      cdiv(nnz, kChunk) + 1);
+        BOBA_TIMED("spmv.long", stream,
+                   k_spmv_chunks<<<g, kChunkBlock, 0, stream>>>(row_ptr, col, val, x, cnt, list, cap,
+                                                                cstart, partial));
+        BOBA_TIMED("spmv.long", stream,
+                   k_spmv_gather<<<8, 256, 0, stream>>>(cnt, list, cap, cstart, partial, y));
+    }
+    BOBA_LAUNCH_CHECK();
+    return BOBA_OK;
+}
