@@ -51,9 +51,17 @@ __device__ __forceinline__ uint64_t globaltimer_ns()
 }
 
 // ---------------------------------------------------------------------------
-// block-wide exclusive scan of one uint32 per thread (blockDim.x == BLOCK)
+// block-wide exclusive scan of one uint32 per thread (blockDim.x == BLOCK);
+// Op is + (default) or max, both with identity 0.
 // ---------------------------------------------------------------------------
-template <int BLOCK>
+struct OpSum32 {
+    __device__ __forceinline__ static uint32_t apply(uint32_t a, uint32_t b) { return a + b; }
+};
+struct OpMax32 {
+    __device__ __forceinline__ static uint32_t apply(uint32_t a, uint32_t b) { return a > b ? a : b; }
+};
+
+template <int BLOCK, class Op = OpSum32>
 struct BlockScan {
     static_assert(BLOCK % 32 == 0 && BLOCK <= 1024, "block size");
     static constexpr int kWarps = BLOCK / 32;
@@ -71,8 +79,10 @@ struct BlockScan {
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t y = __shfl_up_sync(kFull, inc, o);
-            if (lane >= o) inc += y;
+            if (lane >= o) inc = Op::apply(inc, y);
         }
+        uint32_t exc = __shfl_up_sync(kFull, inc, 1);
+        if (lane == 0) exc = 0;
         if (lane == 31) sm.warp_sums[warp] = inc;
         __syncthreads();
         if (warp == 0) {
@@ -81,13 +91,15 @@ struct BlockScan {
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 uint32_t y = __shfl_up_sync(kFull, wi, o);
-                if (lane >= o) wi += y;
+                if (lane >= o) wi = Op::apply(wi, y);
             }
-            if (lane < kWarps) sm.warp_sums[lane] = wi - w;   // exclusive warp offsets
+            uint32_t we = __shfl_up_sync(kFull, wi, 1);
+            if (lane == 0) we = 0;
+            if (lane < kWarps) sm.warp_sums[lane] = we;   // exclusive warp offsets
             if (lane == 31) sm.total = wi;
         }
         __syncthreads();
-        uint32_t r = sm.warp_sums[warp] + inc - x;
+        const uint32_t r = Op::apply(sm.warp_sums[warp], exc);
         *total = sm.total;
         return r;
     }
@@ -112,8 +124,17 @@ constexpr uint64_t kFlagMask = 3ull << 62;
 constexpr uint64_t kValMask = ~kFlagMask;
 constexpr uint64_t kTimeoutNs = 2000000000ull;   // 2 s
 
+struct OpSum {
+    __device__ __forceinline__ static uint64_t apply(uint64_t a, uint64_t b) { return a + b; }
+};
+struct OpMax {
+    __device__ __forceinline__ static uint64_t apply(uint64_t a, uint64_t b) { return a > b ? a : b; }
+};
+
 // Called by all 32 lanes of ONE warp.  Returns the exclusive prefix of tile
-// `tile` (same value in every lane) and publishes its inclusive prefix.
+// `tile` under Op (same value in every lane; the identity, 0, for tile 0) and
+// publishes its inclusive prefix.  Values must fit in 62 bits.
+template <class Op = OpSum>
 __device__ __forceinline__ uint64_t lookback_exclusive(uint64_t *tstat, int64_t tile, uint64_t agg,
                                                        uint32_t *status)
 {
@@ -151,12 +172,12 @@ __device__ __forceinline__ uint64_t lookback_exclusive(uint64_t *tstat, int64_t 
         const int first = pre ? (__ffs(pre) - 1) : 31;
         uint64_t c = (lane <= first) ? (s & kValMask) : 0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
-        prefix += c;
+        for (int o = 16; o > 0; o >>= 1) c = Op::apply(c, __shfl_xor_sync(kFull, c, o));
+        prefix = Op::apply(prefix, c);
         if (pre) break;
         base -= 32;
     }
-    if (lane == 0) st_relaxed_u64(&tstat[tile], kFlagPre | ((prefix + agg) & kValMask));
+    if (lane == 0) st_relaxed_u64(&tstat[tile], kFlagPre | (Op::apply(prefix, agg) & kValMask));
     return prefix;
 }
 

@@ -12,18 +12,19 @@
 //                   scatter staged through shared memory so that runs of equal
 //                   digits are written contiguously (Adinets and Merrill,
 //                   "Onesweep", 2022, for the single-pass scheme)
-//   k_csr_finish    row_ptr from the boundaries of the sorted keys and
+//   k_csr_ends      ends[k] = one past the last sorted entry of row k, and
 //                   val = fp32(1 / outdeg(col))
+//   k_csr_rowptr    row_ptr[v+1] = max over u <= v of ends[u] (a single-pass
+//                   max-scan with decoupled look-back), row_ptr[0] = 0
 #include "common.cuh"
 #include "host.hpp"
 
 namespace boba {
 namespace {
 
-constexpr int kPassBlock = 256;
-constexpr int kPassItems = 16;                       // per thread
+constexpr int kPassBlock = 512;
+constexpr int kPassItems = 8;                        // per thread
 constexpr int kPassTile = kPassBlock * kPassItems;  // 4096 items
-constexpr int kWarps = kPassBlock / 32;
 constexpr int kMaxPasses = 4;                        // 32-bit keys
 constexpr int kNumCtr = 16;
 
@@ -36,10 +37,14 @@ __device__ __forceinline__ uint64_t pass_flag(int p, bool inclusive)
 }
 constexpr uint64_t kPassValMask = (1ull << 60) - 1;
 
+constexpr int kRowTile = 1024;                       // vertices per row_ptr scan tile
+constexpr int kCtrRowTicket = 8;
+
 struct CsrLayout {
     int passes;
-    int64_t tiles;
-    size_t kA, vA, kB, vB, outdeg, hist, dstart, status, counters, total, zero_begin, zero_end;
+    int64_t tiles, row_tiles;
+    size_t kA, vA, kB, vB, outdeg, hist, dstart, status, counters, ends, rstat, total, zero_begin,
+        zero_end;
 };
 
 bool csr_layout(int64_t m, int64_t n, CsrLayout &L)
@@ -49,6 +54,7 @@ bool csr_layout(int64_t m, int64_t n, CsrLayout &L)
     while (bits < 31 && (1ll << bits) < n) bits++;
     L.passes = (bits + 7) / 8;
     L.tiles = cdiv(m > 0 ? m : 1, kPassTile);
+    L.row_tiles = cdiv(n > 0 ? n : 1, kRowTile);
     const size_t mm = (size_t)(m > 0 ? m : 1);
     Carve c;
     L.kA = c.take(mm * 4);
@@ -60,6 +66,8 @@ bool csr_layout(int64_t m, int64_t n, CsrLayout &L)
     L.hist = c.take(kMaxPasses * 256 * 4);
     L.status = c.take((size_t)L.tiles * 256 * 8);
     L.counters = c.take(kNumCtr * 4);
+    L.ends = c.take((size_t)L.row_tiles * kRowTile * 4);
+    L.rstat = c.take((size_t)L.row_tiles * 8);
     L.zero_end = c.off;
     L.dstart = c.take(kMaxPasses * 256 * 4);
     L.total = c.off;
@@ -110,34 +118,41 @@ __global__ void __launch_bounds__(256) k_csr_digits(const uint32_t *__restrict__
     }
 }
 
-// One stable LSD pass over digit p (bits 8p .. 8p+7).
-__global__ void __launch_bounds__(kPassBlock) k_csr_pass(
+// One stable LSD pass over digit p (bits 8p .. 8p+7).  BLOCK threads hold
+// ITEMS items each; the first 256 threads also own one digit each for the
+// cross-tile look-back.
+template <int BLOCK, int ITEMS>
+__global__ void __launch_bounds__(BLOCK) k_csr_pass(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t m, int p, const uint32_t *__restrict__ dstart,
     uint64_t *status_lb, uint32_t *counters, uint32_t *status)
 {
-    __shared__ uint32_t s_keys[kPassTile];
-    __shared__ uint32_t s_vals[kPassTile];
-    __shared__ uint16_t s_wcnt[kWarps][256];      // per-warp digit counts, then warp prefixes
-    __shared__ uint32_t s_tpre[256];               // tile-local exclusive digit offsets
-    __shared__ uint32_t s_base[256];               // global start of this tile's run of digit d
-    __shared__ typename BlockScan<256>::Smem sm;
+    constexpr int TILE = BLOCK * ITEMS;
+    constexpr int WARPS = BLOCK / 32;
+    constexpr int WARP_ITEMS = 32 * ITEMS;
+    static_assert(BLOCK >= 256, "one thread per digit");
+    __shared__ uint32_t s_keys[TILE];
+    __shared__ uint32_t s_vals[TILE];
+    __shared__ uint16_t s_wcnt[WARPS][256];      // per-warp digit counts, then warp prefixes
+    __shared__ uint32_t s_tpre[256];              // tile-local exclusive digit offsets
+    __shared__ uint32_t s_base[256];              // global start of this tile's run of digit d
+    __shared__ typename BlockScan<BLOCK>::Smem sm;
     __shared__ uint32_t s_tile;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_tile = atomicAdd(&counters[p], 1u);
-    for (int i = threadIdx.x; i < kWarps * 256; i += kPassBlock) (&s_wcnt[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < WARPS * 256; i += BLOCK) (&s_wcnt[0][0])[i] = 0;
     __syncthreads();
     const int64_t tile = s_tile;
-    const int64_t t0 = tile * kPassTile;
+    const int64_t t0 = tile * TILE;
     const int shift = 8 * p;
 
-    // load: item (warp, k, lane) is tile index warp*512 + k*32 + lane, so the
-    // k-major / lane-minor processing order of a warp is the input order
-    uint32_t key[kPassItems], val[kPassItems], rank[kPassItems];
+    // load: item (warp, k, lane) is tile index warp*WARP_ITEMS + k*32 + lane, so
+    // the k-major / lane-minor processing order of a warp is the input order
+    uint32_t key[ITEMS], val[ITEMS], rank[ITEMS];
 #pragma unroll
-    for (int k = 0; k < kPassItems; ++k) {
-        const int64_t i = t0 + warp * (32 * kPassItems) + k * 32 + lane;
+    for (int k = 0; k < ITEMS; ++k) {
+        const int64_t i = t0 + warp * WARP_ITEMS + k * 32 + lane;
         if (i < m) {
             key[k] = __ldcs(kin + i);
             val[k] = __ldcs(vin + i);
@@ -148,8 +163,8 @@ __global__ void __launch_bounds__(kPassBlock) k_csr_pass(
     }
     const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
-    for (int k = 0; k < kPassItems; ++k) {
-        const int64_t i = t0 + warp * (32 * kPassItems) + k * 32 + lane;
+    for (int k = 0; k < ITEMS; ++k) {
+        const int64_t i = t0 + warp * WARP_ITEMS + k * 32 + lane;
         const bool valid = i < m;
         const uint32_t d = valid ? ((key[k] >> shift) & 255u) : 256u;
         const unsigned peers = __match_any_sync(kFull, d);
@@ -164,55 +179,70 @@ __global__ void __launch_bounds__(kPassBlock) k_csr_pass(
         __syncwarp();
     }
     __syncthreads();
-    // digit d = threadIdx.x: tile count, warp prefixes, tile-local offsets
+    // digit d = threadIdx.x (< 256): tile count, warp prefixes, tile-local offsets
     const int d = threadIdx.x;
     uint32_t cnt = 0;
+    if (d < 256) {
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-        const uint32_t c = s_wcnt[w][d];
-        s_wcnt[w][d] = (uint16_t)cnt;
-        cnt += c;
+        for (int w = 0; w < WARPS; ++w) {
+            const uint32_t c = s_wcnt[w][d];
+            s_wcnt[w][d] = (uint16_t)cnt;
+            cnt += c;
+        }
     }
     uint32_t tot;
-    const uint32_t tpre = BlockScan<256>::exclusive(cnt, &tot, sm);
-    s_tpre[d] = tpre;
-
-    // per-digit look-back across tiles (thread d owns digit d)
-    {
+    const uint32_t tpre = BlockScan<BLOCK>::exclusive(cnt, &tot, sm);
+    if (d < 256) {
+        s_tpre[d] = tpre;
+        // per-digit look-back across tiles, reading 8 predecessors per round trip
         uint64_t *st = status_lb + tile * 256 + d;
         if (tile == 0) {
             st_relaxed_u64(st, pass_flag(p, true) | cnt);
             s_base[d] = dstart[p * 256 + d];
         } else {
             st_relaxed_u64(st, pass_flag(p, false) | cnt);
+            const uint64_t fa = pass_flag(p, false), fp = pass_flag(p, true);
             uint64_t excl = 0;
             int64_t t = tile - 1;
             uint64_t tstart = 0;
             uint32_t spins = 0;
             while (t >= 0) {
-                const uint64_t s = ld_relaxed_u64(status_lb + t * 256 + d);
-                const uint64_t f = s & ~kPassValMask;
-                if (f == pass_flag(p, true)) { excl += s & kPassValMask; break; }
-                if (f == pass_flag(p, false)) { excl += s & kPassValMask; --t; continue; }
-                if ((++spins & 255u) == 1u) {
-                    const uint64_t now = globaltimer_ns();
-                    if (tstart == 0) tstart = now;
-                    else if (now - tstart > kTimeoutNs) {
-                        raise_status(status, BOBA_ERR_TIMEOUT);
-                        break;
-                    }
+                uint64_t w[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    w[j] = (t - j >= 0) ? ld_relaxed_u64(status_lb + (t - j) * 256 + d) : fp;
+                int used = 0;
+                bool done = false;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (done || used != j) continue;
+                    const uint64_t f = w[j] & ~kPassValMask;
+                    if (f == fp) { excl += w[j] & kPassValMask; done = true; }
+                    else if (f == fa) { excl += w[j] & kPassValMask; ++used; }
                 }
-                __nanosleep(32);
+                if (done) break;
+                t -= used;
+                if (used == 0) {
+                    if ((++spins & 255u) == 1u) {
+                        const uint64_t now = globaltimer_ns();
+                        if (tstart == 0) tstart = now;
+                        else if (now - tstart > kTimeoutNs) {
+                            raise_status(status, BOBA_ERR_TIMEOUT);
+                            break;
+                        }
+                    }
+                    __nanosleep(32);
+                }
             }
-            st_relaxed_u64(st, pass_flag(p, true) | ((excl + cnt) & kPassValMask));
+            st_relaxed_u64(st, fp | ((excl + cnt) & kPassValMask));
             s_base[d] = dstart[p * 256 + d] + (uint32_t)excl;
         }
     }
     __syncthreads();
     // stage the tile in shared memory in sorted order
 #pragma unroll
-    for (int k = 0; k < kPassItems; ++k) {
-        const int64_t i = t0 + warp * (32 * kPassItems) + k * 32 + lane;
+    for (int k = 0; k < ITEMS; ++k) {
+        const int64_t i = t0 + warp * WARP_ITEMS + k * 32 + lane;
         if (i < m) {
             const uint32_t dd = (key[k] >> shift) & 255u;
             const uint32_t pos = s_tpre[dd] + s_wcnt[warp][dd] + rank[k];
@@ -222,10 +252,10 @@ __global__ void __launch_bounds__(kPassBlock) k_csr_pass(
     }
     __syncthreads();
     // write out: consecutive threads write consecutive slots of a digit run
-    const int64_t valid_n = (m - t0) < kPassTile ? (m - t0) : kPassTile;
+    const int64_t valid_n = (m - t0) < TILE ? (m - t0) : TILE;
 #pragma unroll
-    for (int k = 0; k < kPassItems; ++k) {
-        const int j = k * kPassBlock + threadIdx.x;
+    for (int k = 0; k < ITEMS; ++k) {
+        const int j = k * BLOCK + threadIdx.x;
         if (j < valid_n) {
             const uint32_t kk = s_keys[j];
             const uint32_t dd = (kk >> shift) & 255u;
@@ -236,28 +266,59 @@ __global__ void __launch_bounds__(kPassBlock) k_csr_pass(
     }
 }
 
-// row_ptr[v] = number of sorted keys < v; val[i] = fp32(1 / outdeg(col[i])).
-__global__ void __launch_bounds__(256) k_csr_finish(const uint32_t *__restrict__ skeys,
-                                                    const int32_t *__restrict__ col, int64_t m,
-                                                    int64_t n, const uint32_t *__restrict__ outdeg,
-                                                    int64_t *__restrict__ row_ptr,
-                                                    float *__restrict__ val)
+// ends[k] = 1 + index of the last sorted entry with key k (0 if none);
+// val[i] = fp32(1 / outdeg(col[i])), correctly rounded.
+__global__ void __launch_bounds__(256) k_csr_ends(const uint32_t *__restrict__ skeys,
+                                                  const int32_t *__restrict__ col, int64_t m,
+                                                  uint32_t n, const uint32_t *__restrict__ outdeg,
+                                                  uint32_t *__restrict__ ends,
+                                                  float *__restrict__ val)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        const int64_t k = skeys[i] < (uint32_t)n ? (int64_t)skeys[i] : n;
-        const int64_t prev = i == 0 ? -1 : (skeys[i - 1] < (uint32_t)n ? (int64_t)skeys[i - 1] : n);
-        for (int64_t v = prev + 1; v <= k && v <= n; ++v) row_ptr[v] = i;
-        if (i == m - 1)
-            for (int64_t v = k + 1; v <= n; ++v) row_ptr[v] = m;
-        const uint32_t c = (uint32_t)col[i];
-        const uint32_t dg = c < (uint32_t)n ? __ldg(outdeg + c) : 0u;
+        const uint32_t k = skeys[i];
+        if (k < n && (i == m - 1 || skeys[i + 1] != k)) ends[k] = (uint32_t)(i + 1);
+        const uint32_t c = (uint32_t)__ldcs(col + i);
+        const uint32_t dg = c < n ? __ldg(outdeg + c) : 0u;
         float r;
         if (dg == 0) r = 0.0f;
         else if (dg < (1u << 24)) r = __frcp_rn((float)dg);      // exact operand, IEEE rounding
         else r = (float)(1.0 / (double)dg);
         __stcs(val + i, r);
     }
+}
+
+// row_ptr[0] = 0, row_ptr[v+1] = max over u <= v of ends[u]: an inclusive
+// max-scan, single pass with decoupled look-back over vertex tiles.
+__global__ void __launch_bounds__(256) k_csr_rowptr(const uint32_t *__restrict__ ends, int64_t n,
+                                                    int64_t *__restrict__ row_ptr, uint64_t *tstat,
+                                                    uint32_t *counters, uint32_t *status)
+{
+    __shared__ typename BlockScan<256, OpMax32>::Smem sm;
+    __shared__ uint32_t s_tile;
+    __shared__ uint64_t s_prefix;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&counters[kCtrRowTicket], 1u);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    const int64_t v0 = tile * kRowTile + 4 * (int64_t)threadIdx.x;
+    const uint4 e = *reinterpret_cast<const uint4 *>(ends + v0);    // padded, zero beyond n
+    uint32_t run[4];
+    run[0] = e.x;
+    run[1] = max(run[0], e.y);
+    run[2] = max(run[1], e.z);
+    run[3] = max(run[2], e.w);
+    uint32_t tot;
+    const uint32_t ex = BlockScan<256, OpMax32>::exclusive(run[3], &tot, sm);
+    if (threadIdx.x < 32) {
+        const uint64_t p = lookback_exclusive<OpMax>(tstat, tile, tot, status);
+        if (threadIdx.x == 0) s_prefix = p;
+    }
+    __syncthreads();
+    const uint32_t pre = max((uint32_t)s_prefix, ex);
+    if (tile == 0 && threadIdx.x == 0) row_ptr[0] = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (v0 + j < n) row_ptr[v0 + j + 1] = (int64_t)max(pre, run[j]);
 }
 
 __global__ void k_rowptr_zero(int64_t *row_ptr, int64_t n)
@@ -333,16 +394,20 @@ extern "C" boba_status_t boba_coo_to_csr(const int32_t *src, const int32_t *dst,
         uint32_t *ko = (p & 1) ? kB : kA;
         uint32_t *vo = last ? reinterpret_cast<uint32_t *>(col_out) : ((p & 1) ? vB : vA);
         BOBA_TIMED("csr.pass", stream,
-                   k_csr_pass<<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
+                   k_csr_pass<kPassBlock, kPassItems><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
                        kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status));
         kin = ko;
         vin = vo;
     }
     {
-        const int g = persistent_grid((const void *)k_csr_finish, 256, cdiv(m, 256));
+        uint32_t *ends = reinterpret_cast<uint32_t *>(b + L.ends);
+        const int g = persistent_grid((const void *)k_csr_ends, 256, cdiv(m, 256));
         BOBA_TIMED("csr.finish", stream,
-                   k_csr_finish<<<g, 256, 0, stream>>>(kin, col_out, m, n, outdeg, row_ptr,
-                                                       val_out));
+                   k_csr_ends<<<g, 256, 0, stream>>>(kin, col_out, m, nn, outdeg, ends, val_out));
+        BOBA_TIMED("csr.finish", stream,
+                   k_csr_rowptr<<<(unsigned)L.row_tiles, 256, 0, stream>>>(
+                       ends, n, row_ptr, reinterpret_cast<uint64_t *>(b + L.rstat), ctr,
+                       dev->status));
     }
     BOBA_LAUNCH_CHECK();
     return BOBA_OK;
