@@ -5,8 +5,7 @@
 //                  short average row length several rows share a warp).  Lane j
 //                  of a group sums entries j, j+LPR, ... with FMA; the group then
 //                  reduces with a fixed xor tree.  Rows longer than kLongRow are
-//                  set aside in a list.  A warp works on 32 consecutive rows,
-//                  four rows per lane group in flight.
+//                  set aside in a list.
 //   k_spmv_plan    one block: chunk offsets of the long rows (kChunk entries each)
 //   k_spmv_chunks  one 1024-thread block per chunk: strided FMA sums and a
 //                  fixed-order block reduction into partial[chunk]
@@ -44,11 +43,6 @@ bool spmv_layout(int64_t n_rows, int64_t nnz, SpmvLayout &L)
     return true;
 }
 
-// A warp takes 32 consecutive rows at a time: one coalesced load of their row
-// pointers, then LPR rounds of RPW = 32/LPR rows, four rounds interleaved so
-// that each lane group has four rows' loads in flight.  Lane j of a group sums
-// entries j, j+LPR, j+2LPR, ... of its row with FMA, then the group reduces
-// with a fixed xor tree: the order depends only on the row's own entries.
 template <int LPR>
 __global__ void __launch_bounds__(kRowsBlock) k_spmv_rows(
     const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
@@ -56,62 +50,33 @@ __global__ void __launch_bounds__(kRowsBlock) k_spmv_rows(
     int64_t n_rows, uint32_t *long_count, uint32_t *long_list, uint32_t cap, uint32_t *status)
 {
     constexpr int RPW = 32 / LPR;
-    constexpr int IL = LPR >= 4 ? 4 : LPR;          // rounds interleaved
     const int lane = threadIdx.x & 31;
-    const int gl = lane % LPR, grp = lane / LPR;
+    const int gl = lane % LPR;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t rb = warp * 32; rb < n_rows; rb += nwarps * 32) {
-        const int64_t rl = rb + lane;
-        const int64_t b = __ldg(row_ptr + (rl < n_rows ? rl : n_rows));
-        int64_t e = __shfl_down_sync(kFull, b, 1);
-        if (lane == 31) e = __ldg(row_ptr + (rl + 1 < n_rows ? rl + 1 : n_rows));
-        if (rl >= n_rows) e = b;                        // rows past the end are empty
-        for (int round = 0; round < LPR; round += IL) {
-            int64_t beg[IL], len[IL];
-            float acc[IL];
-            int64_t maxlen = 0;
+    for (int64_t rb = warp * RPW; rb < n_rows; rb += nwarps * RPW) {
+        const int64_t r = rb + lane / LPR;
+        int64_t beg = 0, end = 0;
+        if (r < n_rows) {
+            beg = __ldg(row_ptr + r);
+            end = __ldg(row_ptr + r + 1);
+        }
+        const bool is_long = end - beg > kLongRow;
+        float acc = 0.0f;
+        if (!is_long) {
+#pragma unroll 4
+            for (int64_t p = beg + gl; p < end; p += LPR)
+                acc = fmaf(__ldcs(val + p), __ldg(x + __ldcs(col + p)), acc);
+        }
 #pragma unroll
-            for (int u = 0; u < IL; ++u) {
-                const int q = (round + u) * RPW + grp;          // row within the batch
-                beg[u] = __shfl_sync(kFull, b, q);
-                len[u] = __shfl_sync(kFull, e, q) - beg[u];
-                if (len[u] > kLongRow) len[u] = 0;              // deferred to the long path
-                acc[u] = 0.0f;
-                maxlen = max(maxlen, len[u]);
-            }
-            for (int64_t off = gl; off < maxlen; off += LPR) {
-                int32_t c[IL];
-                float v[IL];
-#pragma unroll
-                for (int u = 0; u < IL; ++u) {
-                    const bool ok = off < len[u];
-                    c[u] = ok ? __ldcs(col + beg[u] + off) : -1;
-                    v[u] = ok ? __ldcs(val + beg[u] + off) : 0.0f;
-                }
-#pragma unroll
-                for (int u = 0; u < IL; ++u)
-                    if (c[u] >= 0) acc[u] = fmaf(v[u], __ldg(x + c[u]), acc[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < IL; ++u) {
-#pragma unroll
-                for (int o = LPR / 2; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(kFull, acc[u], o);
-            }
-#pragma unroll
-            for (int u = 0; u < IL; ++u) {
-                const int q = (round + u) * RPW + grp;
-                const int64_t r = rb + q;
-                const int64_t fulllen = __shfl_sync(kFull, e, q) - __shfl_sync(kFull, b, q);
-                if (gl == 0 && r < n_rows) {
-                    if (fulllen <= kLongRow) {
-                        y[r] = acc[u];
-                    } else {
-                        const uint32_t i = atomicAdd(long_count, 1u);
-                        if (i < cap) long_list[i] = (uint32_t)r;
-                        else raise_status(status, BOBA_ERR_INVALID_ARG);
-                    }
-                }
+        for (int o = LPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if (gl == 0 && r < n_rows) {
+            if (!is_long) {
+                y[r] = acc;
+            } else {
+                const uint32_t i = atomicAdd(long_count, 1u);
+                if (i < cap) long_list[i] = (uint32_t)r;
+                else raise_status(status, BOBA_ERR_INVALID_ARG);   // row_ptr inconsistent with nnz
             }
         }
     }
@@ -198,7 +163,8 @@ void launch_rows(const int64_t *row_ptr, const int32_t *col, const float *val, c
                  float *y, int64_t n_rows, uint32_t *cnt, uint32_t *list, uint32_t cap,
                  uint32_t *status, cudaStream_t stream)
 {
-    const int64_t warps = cdiv(n_rows, 32);
+    constexpr int RPW = 32 / LPR;
+    const int64_t warps = cdiv(n_rows, RPW);
     const int g = persistent_grid((const void *)k_spmv_rows<LPR>, kRowsBlock,
                                   cdiv(warps, kRowsBlock / 32));
     BOBA_TIMED("spmv", stream,
