@@ -294,6 +294,11 @@ def run_ours(args):
     e2e = None if args.no_e2e else run_e2e(args, boba, torch, dev, stream, src_h, dst_h, m, n,
                                            world)
 
+    batched = None
+    if args.batched and world == 1:
+        del src_h, dst_h
+        batched = run_batched(args, boba, torch, dev, stream, flush, n_batch=args.batch_graphs)
+
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": "Gedges/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 4),
@@ -313,6 +318,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": e2e,
+        "batched": batched,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w, args)
@@ -353,6 +359,96 @@ def compare_orders(args, boba, torch, dev, stream, src, dst, so, do, m, n, row_p
     out["csr_speedup_boba_vs_random"] = round(out["random"]["csr_ms"] / out["boba"]["csr_ms"], 3)
     out["spmv_bytes_per_launch"] = spmv_bytes
     return out
+
+
+def run_batched(args, boba, torch, dev, stream, flush, n_batch=4096, seed=None):
+    """The batched workload: n_batch R-MAT graphs (n log-uniform in [2^8, 2^18),
+    edge factor 4..32) reordered in one persistent launch, against one launch
+    sequence per graph (eager, and replayed from a CUDA graph).  Outputs of the
+    two forms are compared bit for bit."""
+    import synth
+    seed = synth.SEED_BASE + 3 if seed is None else seed
+    n_g, m_g = synth.batch_sizes(n_batch, seed)
+    eo = np.zeros(n_batch + 1, np.int64); eo[1:] = np.cumsum(m_g)
+    vo = np.zeros(n_batch + 1, np.int64); vo[1:] = np.cumsum(n_g)
+    E, V = int(eo[-1]), int(vo[-1])
+    src_h = torch.empty(E, dtype=torch.int32, pin_memory=True)
+    dst_h = torch.empty(E, dtype=torch.int32, pin_memory=True)
+    synth.rmat_batch(n_batch, seed, out=(src_h.numpy(), dst_h.numpy()))
+    src, dst = src_h.to(dev), dst_h.to(dev)
+    del src_h, dst_h
+    eo_d, vo_d = torch.from_numpy(eo).to(dev), torch.from_numpy(vo).to(dev)
+    max_m, max_n = int(m_g.max()), int(n_g.max())
+    perm = torch.empty(V, dtype=torch.int32, device=dev)
+    so, do = torch.empty_like(src), torch.empty_like(dst)
+    ws = torch.empty(boba.boba_reorder_batched_workspace_bytes(n_batch, max_m, max_n),
+                     dtype=torch.uint8, device=dev)
+
+    def batched(st):
+        boba.check(boba.boba_reorder_batched(src, dst, eo_d, vo_d, n_batch, max_m, max_n, E, V,
+                                             perm, so, do, ws, ws.numel(), st), "batched")
+
+    # one launch sequence per graph, outputs into separate buffers
+    perm1 = torch.empty_like(perm)
+    so1, do1 = torch.empty_like(src), torch.empty_like(dst)
+    ws1 = torch.empty(boba.boba_reorder_workspace_bytes(max_m, max_n), dtype=torch.uint8,
+                      device=dev)
+    views = [(src[eo[g]:eo[g + 1]], dst[eo[g]:eo[g + 1]], int(m_g[g]), int(n_g[g]),
+              perm1[vo[g]:vo[g + 1]], so1[eo[g]:eo[g + 1]], do1[eo[g]:eo[g + 1]])
+             for g in range(n_batch)]
+
+    def per_graph(st):
+        for s_, d_, mg, ng, p_, o1, o2 in views:
+            boba.check(boba.boba_reorder_ex(s_, d_, mg, ng, p_, o1, o2, None, ws1, ws1.numel(),
+                                            st), "per-graph")
+
+    def timed(fn, reps):
+        out = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            out.append(e0.elapsed_time(e1))
+        return statistics.median(out)
+
+    reps = max(3, min(args.steps, 5))
+    for _ in range(args.warmup):
+        batched(stream)
+    t_batched = timed(batched, reps)
+    per_graph(stream)
+    t_pergraph = timed(per_graph, reps)
+    boba.stream_status(stream)
+    identical = bool(torch.equal(perm, perm1) and torch.equal(so, so1) and torch.equal(do, do1))
+
+    # both forms captured once into a CUDA graph and replayed
+    t_graph = {}
+    for name, fn in (("batched", batched), ("per_graph", per_graph)):
+        try:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                fn(torch.cuda.current_stream(dev))
+            torch.cuda.synchronize(dev)
+            for _ in range(2):
+                g.replay()
+            torch.cuda.synchronize(dev)
+            t_graph[name] = round(timed(lambda st, g=g: g.replay(), reps), 3)
+            del g
+        except Exception as exc:                 # report why capture was not possible
+            t_graph[name] = "capture failed: " + str(exc)[:160]
+    boba.stream_status(stream)
+    identical = identical and bool(torch.equal(perm, perm1) and torch.equal(so, so1))
+    return {"workload": f"rmat_batch{n_batch}", "graphs": n_batch, "edges": E, "vertices": V,
+            "max_m": max_m, "max_n": max_n,
+            "batched_ms": round(t_batched, 3),
+            "batched_gedges_s": round(E / (t_batched * 1e-3) / 1e9, 3),
+            "per_graph_ms": round(t_pergraph, 3),
+            "per_graph_gedges_s": round(E / (t_pergraph * 1e-3) / 1e9, 3),
+            "speedup_batched_vs_per_graph": round(t_pergraph / t_batched, 3),
+            "cuda_graph_ms": t_graph,
+            "bit_identical": identical}
 
 
 def run_e2e(args, boba, torch, dev, stream, src_h, dst_h, m, n, world):
@@ -477,6 +573,9 @@ def main():
     ap.add_argument("--cpu-sample-edges", type=int, default=1 << 27)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batched", type=int, default=1,
+                    help="1: also time the batched workload (4096 graphs) vs per-graph launches")
+    ap.add_argument("--batch-graphs", type=int, default=4096)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)        # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -144,27 +144,31 @@ boba_status_t boba_reorder_static(const int32_t *src, const int32_t *dst, int64_
 
 /*
  * boba_reorder_batched -- BOBA (as boba_reorder) for G independent graphs
- * packed back to back, in one persistent kernel launch.
+ * packed back to back, in one persistent kernel launch (after a one-block
+ * planning kernel).
  *
- *   src, dst     int32[E]  packed COO, E = edge_off[G]; graph g owns edges
+ *   src, dst     int32[total_m] packed COO; graph g owns edges
  *                [edge_off[g], edge_off[g+1]) with LOCAL vertex IDs in
  *                [0, vert_off[g+1] - vert_off[g])                   (device)
- *   edge_off     int64[G+1], edge_off[0] = 0, non-decreasing          (device)
- *   vert_off     int64[G+1], vert_off[0] = 0, non-decreasing          (device)
+ *   edge_off     int64[G+1], non-decreasing, edge_off[G] <= total_m   (device)
+ *   vert_off     int64[G+1], non-decreasing, vert_off[G] <= total_n   (device)
  *   G            number of graphs, >= 0
- *   max_m, max_n upper bounds on any one graph's edges and vertices, each
- *                <= 2^31 - 1 (used only to validate and size scratch)
- *   total_m, total_n  edge_off[G] and vert_off[G] (the host must know them to
- *                size the outputs; they are not read back from the device)
+ *   max_m, max_n upper bounds on any one graph's edges (<= 2^31 - 1) and
+ *                vertices (<= 442,368 = 8 x 55,296: a graph's key array must
+ *                fit in the shared memory of one 8-CTA cluster)
+ *   total_m, total_n  sizes of the packed arrays (host-known)
  *   perm_out     int32[total_n], packed by vert_off, local labels    (device)
- *   src_out, dst_out int32[total_m], packed by edge_off, local labels; may
- *                alias src, dst                                        (device)
- *   ws, ws_bytes scratch of boba_reorder_batched_workspace_bytes(...) bytes
+ *   src_out, dst_out int32[total_m], packed by edge_off, local labels (device)
+ *   ws, ws_bytes scratch of boba_reorder_batched_workspace_bytes(G, max_m,
+ *                max_n) bytes, 256-byte aligned
  *
- * The per-graph result equals boba_reorder on that graph alone, bit for bit.
- * Offsets that are not monotone or exceed the totals raise
- * BOBA_ERR_INVALID_ARG in the status word and the bad graphs are skipped.
- * Never allocates; safe to capture in a CUDA graph.
+ * Each graph's result equals boba_reorder on that graph alone, bit for bit.
+ * A graph up to 55,296 vertices is reordered by one CTA in its shared memory;
+ * a larger one by an 8-CTA cluster sharing the key array through distributed
+ * shared memory.  Work is claimed largest graph first.  A graph whose offsets
+ * are inconsistent or exceed max_m / max_n is skipped and raises
+ * BOBA_ERR_INVALID_ARG in the status word.  Never allocates; safe to capture
+ * in a CUDA graph.  src_out/dst_out must not alias src/dst.
  */
 boba_status_t boba_reorder_batched(const int32_t *src, const int32_t *dst,
                                    const int64_t *edge_off, const int64_t *vert_off,
@@ -173,7 +177,8 @@ boba_status_t boba_reorder_batched(const int32_t *src, const int32_t *dst,
                                    int32_t *perm_out, int32_t *src_out, int32_t *dst_out,
                                    void *ws, size_t ws_bytes, void *stream);
 
-size_t boba_reorder_batched_workspace_bytes(int64_t G, int64_t total_m, int64_t total_n);
+/* Scratch bytes for boba_reorder_batched on the current device (0 if invalid). */
+size_t boba_reorder_batched_workspace_bytes(int64_t G, int64_t max_m, int64_t max_n);
 
 /* ------------------------------------------------------------------------
  * Measurement path: COO -> CSR and SpMV (Alg. 3, Sec. 1.2.2)

@@ -13,7 +13,7 @@ import torch
 from ._lib import BobaError, STATUS_NAMES, check, load
 
 __all__ = [
-    "BobaError", "load", "reorder", "reorder_perm", "coo_to_csr", "spmv", "stream_status",
+    "BobaError", "load", "reorder", "reorder_perm", "reorder_batched", "coo_to_csr", "spmv", "stream_status",
     "boba_reorder", "boba_reorder_ex", "boba_reorder_workspace_bytes", "boba_reorder_static", "boba_reorder_batched",
     "boba_reorder_batched_workspace_bytes", "boba_coo_to_csr", "boba_coo_to_csr_workspace_bytes",
     "boba_spmv_csr", "boba_spmv_workspace_bytes", "boba_stream_status", "boba_status_string",
@@ -75,8 +75,8 @@ def boba_reorder_batched(src, dst, edge_off, vert_off, G, max_m, max_n, total_m,
                                        _p(dst_out), _p(ws), ws_bytes, _s(stream))
 
 
-def boba_reorder_batched_workspace_bytes(G, total_m, total_n):
-    return load().boba_reorder_batched_workspace_bytes(G, total_m, total_n)
+def boba_reorder_batched_workspace_bytes(G, max_m, max_n):
+    return load().boba_reorder_batched_workspace_bytes(G, max_m, max_n)
 
 
 def boba_coo_to_csr(src, dst, m, n, row_ptr, col_out, val_out, ws, ws_bytes, stream=None):
@@ -169,6 +169,32 @@ def reorder_perm(src, dst, n, *, perm_out=None, label_out=None, ws=None, stream=
     check(boba_reorder_ex(src, dst, m, n, perm_out, None, None, label_out, buf, buf.numel(),
                           stream), "boba_reorder_ex")
     return perm_out
+
+
+def reorder_batched(src, dst, edge_off, vert_off, *, max_m=None, max_n=None, perm_out=None,
+                    src_out=None, dst_out=None, ws=None, stream=None):
+    """BOBA of G packed graphs in one launch: returns (perm, src_out, dst_out), packed.
+
+    ``edge_off``/``vert_off`` are int64 offset arrays (length G+1) on the device;
+    ``max_m``/``max_n`` bound one graph's size (computed on the host if omitted).
+    """
+    _dt(src, torch.int32, "src"); _dt(dst, torch.int32, "dst")
+    _dt(edge_off, torch.int64, "edge_off"); _dt(vert_off, torch.int64, "vert_off")
+    G = edge_off.numel() - 1
+    if max_m is None or max_n is None:
+        eo, vo = edge_off.cpu(), vert_off.cpu()
+        max_m = int((eo[1:] - eo[:-1]).max()) if G > 0 else 0
+        max_n = int((vo[1:] - vo[:-1]).max()) if G > 0 else 0
+    total_m, total_n = src.numel(), int(vert_off[-1].item()) if perm_out is None else perm_out.numel()
+    dev = src.device
+    perm_out = torch.empty(total_n, dtype=torch.int32, device=dev) if perm_out is None else perm_out
+    src_out = torch.empty_like(src) if src_out is None else src_out
+    dst_out = torch.empty_like(dst) if dst_out is None else dst_out
+    buf = _ws(ws, boba_reorder_batched_workspace_bytes(G, max_m, max_n), dev)
+    check(boba_reorder_batched(src, dst, edge_off, vert_off, G, max_m, max_n, total_m, total_n,
+                               perm_out, src_out, dst_out, buf, buf.numel(), stream),
+          "boba_reorder_batched")
+    return perm_out, src_out, dst_out
 
 
 def coo_to_csr(src, dst, n, *, row_ptr=None, col_out=None, val_out=None, ws=None, stream=None):
