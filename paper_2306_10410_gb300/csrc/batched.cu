@@ -34,6 +34,7 @@ constexpr int kBB = 1024;                  // threads per CTA
 constexpr int kTeam = 8;                   // CTAs per cluster, team size for large graphs
 constexpr int kKcap = 54 * 1024;           // vertices per CTA held in shared memory
 constexpr size_t kDynSmem = (size_t)kKcap * 4;
+constexpr int kU = 8;                      // stream loads in flight per thread
 constexpr int kHdrItems = 0, kHdrLarge = 1, kHdrTicket = 2, kHdrValid = 3;
 
 struct BatchArgs {
@@ -150,26 +151,40 @@ __device__ void process_graph(const BatchArgs &a, uint32_t g, int t, int64_t cta
     for (int64_t w = tid; w < Wc; w += kBB) my_bm[w] = 0u;
     team_sync<T>(cl);
 
-    // 2. first occurrence over this member's share of I ++ J
+    // 2. first occurrence over this member's share of I ++ J: kU loads in
+    // flight per thread, then all key reads, then the (rare) atomics
     {
         const int64_t P = 2 * m;
         const int64_t lo = P * t / T, hi = P * (t + 1) / T;
-        for (int64_t b0 = lo + tid; b0 < hi; b0 += 4 * kBB) {
-            int32_t v[4];
+        for (int64_t b0 = lo + tid; b0 < hi; b0 += (int64_t)kU * kBB) {
+            int32_t v[kU];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kU; ++u) {
                 const int64_t i = b0 + (int64_t)u * kBB;
-                v[u] = 0;
+                v[u] = -1;
                 if (i < hi) v[u] = i < m ? __ldcs(a.src + E0 + i) : __ldcs(a.dst + E0 + (i - m));
             }
+            uint32_t own[kU], li[kU], cur[kU];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kU; ++u) {
                 const int64_t i = b0 + (int64_t)u * kBB;
-                if (i >= hi) continue;
-                if ((uint32_t)v[u] >= nn) { raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE); continue; }
-                const uint32_t owner = (uint32_t)v[u] / chunk;
-                uint32_t *p = key_ptr<T>(s_keys, ts, owner) + ((uint32_t)v[u] - owner * chunk);
-                if (*p > (uint32_t)i) atomicMin(p, (uint32_t)i);
+                own[u] = kTeam;                                  // "skip"
+                li[u] = 0;
+                cur[u] = 0;
+                if (i < hi) {
+                    if ((uint32_t)v[u] < nn) {
+                        own[u] = (uint32_t)v[u] / chunk;
+                        li[u] = (uint32_t)v[u] - own[u] * chunk;
+                        cur[u] = key_ptr<T>(s_keys, ts, own[u])[li[u]];
+                    } else {
+                        raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const uint32_t i = (uint32_t)(b0 + (int64_t)u * kBB);
+                if (own[u] < kTeam && cur[u] > i) atomicMin(key_ptr<T>(s_keys, ts, own[u]) + li[u], i);
             }
         }
     }
@@ -269,39 +284,39 @@ __device__ void process_graph(const BatchArgs &a, uint32_t g, int t, int64_t cta
     }
     team_sync<T>(cl);
 
-    // 6. relabel this member's share of the edges
+    // 6. relabel this member's share of the edges: kU/2 edges (kU loads) in
+    // flight per thread, all label reads, then the stores
     {
+        constexpr int U2 = kU / 2;
         const int64_t lo = m * t / T, hi = m * (t + 1) / T;
-        for (int64_t b0 = lo + tid; b0 < hi; b0 += 2 * kBB) {
-            int32_t s[2], d[2];
+        for (int64_t b0 = lo + tid; b0 < hi; b0 += (int64_t)U2 * kBB) {
+            int32_t v[kU];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
+            for (int u = 0; u < U2; ++u) {
                 const int64_t e = b0 + (int64_t)u * kBB;
-                s[u] = d[u] = 0;
+                v[2 * u] = v[2 * u + 1] = -1;
                 if (e < hi) {
-                    s[u] = __ldcs(a.src + E0 + e);
-                    d[u] = __ldcs(a.dst + E0 + e);
+                    v[2 * u] = __ldcs(a.src + E0 + e);
+                    v[2 * u + 1] = __ldcs(a.dst + E0 + e);
+                }
+            }
+            int32_t lab[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                lab[u] = -1;
+                if ((uint32_t)v[u] < nn) {
+                    const uint32_t o = (uint32_t)v[u] / chunk;
+                    lab[u] = (int32_t)key_ptr<T>(s_keys, ts, o)[(uint32_t)v[u] - o * chunk];
                 }
             }
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
+            for (int u = 0; u < U2; ++u) {
                 const int64_t e = b0 + (int64_t)u * kBB;
                 if (e >= hi) continue;
-                int32_t ls = -1, ld = -1;
-                if ((uint32_t)s[u] < nn) {
-                    const uint32_t o = (uint32_t)s[u] / chunk;
-                    ls = (int32_t)key_ptr<T>(s_keys, ts, o)[(uint32_t)s[u] - o * chunk];
-                } else {
+                if (lab[2 * u] < 0 || lab[2 * u + 1] < 0)
                     raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
-                }
-                if ((uint32_t)d[u] < nn) {
-                    const uint32_t o = (uint32_t)d[u] / chunk;
-                    ld = (int32_t)key_ptr<T>(s_keys, ts, o)[(uint32_t)d[u] - o * chunk];
-                } else {
-                    raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
-                }
-                __stcs(a.so + E0 + e, ls);
-                __stcs(a.dout + E0 + e, ld);
+                __stcs(a.so + E0 + e, lab[2 * u]);
+                __stcs(a.dout + E0 + e, lab[2 * u + 1]);
             }
         }
     }
