@@ -381,7 +381,7 @@ def run_batched(args, boba, torch, dev, stream, flush, n_batch=4096, seed=None):
     max_m, max_n = int(m_g.max()), int(n_g.max())
     perm = torch.empty(V, dtype=torch.int32, device=dev)
     so, do = torch.empty_like(src), torch.empty_like(dst)
-    ws = torch.empty(boba.boba_reorder_batched_workspace_bytes(n_batch, max_m, max_n),
+    ws = torch.empty(boba.boba_reorder_batched_workspace_bytes(n_batch, max_m, max_n, E, V),
                      dtype=torch.uint8, device=dev)
 
     def batched(st):

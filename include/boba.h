@@ -160,12 +160,12 @@ boba_status_t boba_reorder_static(const int32_t *src, const int32_t *dst, int64_
  *   perm_out     int32[total_n], packed by vert_off, local labels    (device)
  *   src_out, dst_out int32[total_m], packed by edge_off, local labels (device)
  *   ws, ws_bytes scratch of boba_reorder_batched_workspace_bytes(G, max_m,
- *                max_n) bytes, 256-byte aligned
+ *                max_n, total_m, total_n) bytes, 256-byte aligned
  *
  * Each graph's result equals boba_reorder on that graph alone, bit for bit.
  * A graph up to 55,296 vertices is reordered by one CTA in its shared memory;
- * a larger one by an 8-CTA cluster sharing the key array through distributed
- * shared memory.  Work is claimed largest graph first.  A graph whose offsets
+ * larger ones as boba_batched_set_mode selects.  Work is claimed largest
+ * graph first.  A graph whose offsets
  * are inconsistent or exceed max_m / max_n is skipped and raises
  * BOBA_ERR_INVALID_ARG in the status word.  Never allocates; safe to capture
  * in a CUDA graph.  src_out/dst_out must not alias src/dst.
@@ -178,7 +178,19 @@ boba_status_t boba_reorder_batched(const int32_t *src, const int32_t *dst,
                                    void *ws, size_t ws_bytes, void *stream);
 
 /* Scratch bytes for boba_reorder_batched on the current device (0 if invalid). */
-size_t boba_reorder_batched_workspace_bytes(int64_t G, int64_t max_m, int64_t max_n);
+size_t boba_reorder_batched_workspace_bytes(int64_t G, int64_t max_m, int64_t max_n,
+                                            int64_t total_m, int64_t total_n);
+
+/*
+ * boba_batched_set_mode -- how boba_reorder_batched schedules graphs above
+ * 55,296 vertices: 0 = on 8-CTA clusters with the keys in distributed shared
+ * memory (one persistent cluster launch for everything); 1 = all of them
+ * together, phase by phase, with the keys in global memory, beside a
+ * persistent one-CTA-per-graph launch for the smaller graphs (the default);
+ * -1 = back to the default (or the BOBA_BATCH_MODE environment variable,
+ * "cluster" or "split").  Both give identical results.  Process-wide; host only.
+ */
+void boba_batched_set_mode(int mode);
 
 /* ------------------------------------------------------------------------
  * Measurement path: COO -> CSR and SpMV (Alg. 3, Sec. 1.2.2)

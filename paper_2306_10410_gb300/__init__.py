@@ -15,7 +15,7 @@ from ._lib import BobaError, STATUS_NAMES, check, load
 __all__ = [
     "BobaError", "load", "reorder", "reorder_perm", "reorder_batched", "coo_to_csr", "spmv", "stream_status",
     "boba_reorder", "boba_reorder_ex", "boba_reorder_workspace_bytes", "boba_reorder_static", "boba_reorder_batched",
-    "boba_reorder_batched_workspace_bytes", "boba_coo_to_csr", "boba_coo_to_csr_workspace_bytes",
+    "boba_reorder_batched_workspace_bytes", "boba_batched_set_mode", "boba_coo_to_csr", "boba_coo_to_csr_workspace_bytes",
     "boba_spmv_csr", "boba_spmv_workspace_bytes", "boba_stream_status", "boba_status_string",
     "Workspace", "kernel_timing",
 ]
@@ -75,8 +75,12 @@ def boba_reorder_batched(src, dst, edge_off, vert_off, G, max_m, max_n, total_m,
                                        _p(dst_out), _p(ws), ws_bytes, _s(stream))
 
 
-def boba_reorder_batched_workspace_bytes(G, max_m, max_n):
-    return load().boba_reorder_batched_workspace_bytes(G, max_m, max_n)
+def boba_reorder_batched_workspace_bytes(G, max_m, max_n, total_m, total_n):
+    return load().boba_reorder_batched_workspace_bytes(G, max_m, max_n, total_m, total_n)
+
+
+def boba_batched_set_mode(mode):
+    load().boba_batched_set_mode(int(mode))
 
 
 def boba_coo_to_csr(src, dst, m, n, row_ptr, col_out, val_out, ws, ws_bytes, stream=None):
@@ -190,7 +194,7 @@ def reorder_batched(src, dst, edge_off, vert_off, *, max_m=None, max_n=None, per
     perm_out = torch.empty(total_n, dtype=torch.int32, device=dev) if perm_out is None else perm_out
     src_out = torch.empty_like(src) if src_out is None else src_out
     dst_out = torch.empty_like(dst) if dst_out is None else dst_out
-    buf = _ws(ws, boba_reorder_batched_workspace_bytes(G, max_m, max_n), dev)
+    buf = _ws(ws, boba_reorder_batched_workspace_bytes(G, max_m, max_n, total_m, total_n), dev)
     check(boba_reorder_batched(src, dst, edge_off, vert_off, G, max_m, max_n, total_m, total_n,
                                perm_out, src_out, dst_out, buf, buf.numel(), stream),
           "boba_reorder_batched")

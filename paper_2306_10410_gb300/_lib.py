@@ -36,7 +36,8 @@ SIGNATURES = {
     "boba_reorder_static": (_ST, [_P, _P, _I64, _I64, _P, _P, _P, _P, _P]),
     "boba_reorder_batched": (_ST, [_P, _P, _P, _P, _I64, _I64, _I64, _I64, _I64, _P, _P, _P,
                                    _P, _SZ, _P]),
-    "boba_reorder_batched_workspace_bytes": (_SZ, [_I64, _I64, _I64]),
+    "boba_reorder_batched_workspace_bytes": (_SZ, [_I64, _I64, _I64, _I64, _I64]),
+    "boba_batched_set_mode": (None, [ctypes.c_int]),
     "boba_coo_to_csr": (_ST, [_P, _P, _I64, _I64, _P, _P, _P, _P, _SZ, _P]),
     "boba_coo_to_csr_workspace_bytes": (_SZ, [_I64, _I64]),
     "boba_spmv_csr": (_ST, [_P, _P, _P, _P, _P, _I64, _I64, _P, _SZ, _P]),

@@ -1,25 +1,36 @@
-// Batched BOBA: G independent graphs of uneven sizes in one persistent launch
-// (arXiv 2306.10410, Alg. 2 with AtomicMin, per graph).
+// Batched BOBA: G independent graphs of uneven sizes reordered together
+// (arXiv 2306.10410, Alg. 2 with AtomicMin, per graph).  No work crosses a
+// graph boundary, so graphs need no coordination with each other.
 //
-// Each graph is processed whole by one team of CTAs, so no CTA ever waits on
-// another outside a hardware cluster barrier:
-//   * a graph with at most kKcap vertices is handled by a single CTA; its keys
-//     and then its labels live in that CTA's shared memory;
-//   * a larger graph (up to kTeam * kKcap vertices) is handled by a cluster of
-//     kTeam CTAs; its vertex range is split evenly and each CTA keeps its
-//     slice of the key/label array in its shared memory, which the other CTAs
-//     of the cluster reach through distributed shared memory.
-// Per graph the team runs the same steps as the single-graph path: keys =
-// SENT, first occurrence (atomicMin into shared memory), first-occurrence
-// bitmap (global scratch, resident in L2), its popcount prefix, labels (rank
-// of the key; vertices on no edge after them by ascending ID) written over the
-// keys in place, and the relabel of both endpoint arrays.
+// Two modes (the second is the default; an autotuner can pick either):
 //
-// k_batch_plan orders the work: large graphs first, then small graphs in packs
-// of kTeam (one per CTA of a cluster), each class by decreasing edge count in
-// power-of-two buckets, so that the longest items start first.
+//  kBatchCluster -- one persistent cluster launch.  A graph with at most kKcap
+//     vertices is reordered by a single CTA with its keys, then labels, in that
+//     CTA's shared memory; a larger graph (up to kTeam * kKcap vertices) by a
+//     cluster of kTeam CTAs whose shared memories hold one slice each of the
+//     key/label array, reached through distributed shared memory.  Items are
+//     claimed largest first: large graphs, then packs of kTeam small graphs.
+//
+//  kBatchSplit -- small graphs as above but in a persistent launch without
+//     clusters (every SM takes part), and the graphs above kKcap vertices all
+//     together, phase by phase, in six grid-wide launches with their keys in
+//     global memory: init, first occurrence, mark, bitmap scan, emit,
+//     relabel.  Each phase maps a chunk or tile to its graph by a binary
+//     search over per-graph tile counts; the two look-back scans are segmented
+//     by letting the first tile of each graph publish its prefix at once.
+//     Measured on GB300, distributed shared memory was slower than L2 for the
+//     random key accesses of large graphs, hence this default.
+//
+// In both modes a graph goes through the steps of the single-graph path: keys =
+// SENT, first occurrence, first-occurrence bitmap, popcount prefix, labels
+// (rank of the key; vertices on no edge after them by ascending ID), perm, and
+// the relabel of both endpoint arrays.  k_batch_plan validates the offsets,
+// orders the graphs (large first, each class by decreasing edge count in
+// power-of-two buckets) and tabulates the tiles of the large graphs.
 #include <cooperative_groups.h>
 
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
 
 #include "common.cuh"
@@ -30,24 +41,42 @@ namespace cg = cooperative_groups;
 namespace boba {
 namespace {
 
-constexpr int kBB = 1024;                  // threads per CTA
+constexpr int kBB = 1024;                  // threads per CTA of the per-graph kernels
 constexpr int kTeam = 8;                   // CTAs per cluster, team size for large graphs
 constexpr int kKcap = 54 * 1024;           // vertices per CTA held in shared memory
 constexpr size_t kDynSmem = (size_t)kKcap * 4;
 constexpr int kU = 8;                      // stream loads in flight per thread
-constexpr int kHdrItems = 0, kHdrLarge = 1, kHdrTicket = 2, kHdrValid = 3;
+constexpr int kHdrItems = 0, kHdrLarge = 1, kHdrTicket = 2, kHdrValid = 3, kHdrScanTicket = 4,
+              kHdrEmitTicket = 5;
+
+// tiles of the phase-batched large-graph path
+constexpr int kLB = 256;                   // threads per block
+constexpr int kPosChunk = kLB * 16;        // positions of I ++ J per block step
+constexpr int kVtxTile = kLB * 4;          // vertices per tile
+constexpr int kWordTile = kLB * 8;         // bitmap words per scan tile
+constexpr int kEdgeChunk = kLB * 8;        // edges per relabel block step
+
+enum BatchMode { kBatchCluster = 0, kBatchSplit = 1 };
 
 struct BatchArgs {
     const int32_t *src, *dst;
     const int64_t *eoff, *voff;
     int64_t G, max_m, max_n, total_m, total_n;
     int32_t *perm, *so, *dout;
-    uint32_t *hdr;           // items, large graphs, ticket, valid graphs
+    uint32_t *hdr;           // items, large graphs, ticket, valid graphs, scan/emit tickets
     uint32_t *order;         // graph ids in processing order
-    uint32_t *scratch;       // one region per CTA of the grid
+    uint32_t *scratch;       // one region per CTA of the per-graph kernel
     int64_t region_words;    // wmax bitmap words + wmax/8 group-prefix words
     int64_t wmax;
     uint32_t *status;
+    int large_threshold;     // graphs with more vertices go to the team / phase path
+    // phase-batched large-graph path (prefix tables over the large graphs, L+1 entries)
+    uint32_t *lg_pc, *lg_vt, *lg_wt, *lg_ec, *lg_tot;
+    uint32_t *kl;            // keys, then labels, of the large graphs (vertex-tile padded)
+    uint32_t *lbm;           // bitmaps of the large graphs (word-tile padded)
+    uint32_t *lgrp;          // group prefixes (one per 8 words)
+    uint64_t *lts_scan, *lts_emit;
+    int64_t lts_scan_cap, lts_emit_cap;
 };
 
 __device__ __forceinline__ int floor_log2_p1(int64_t x)   // floor(log2(x + 1)), x >= 0
@@ -55,23 +84,30 @@ __device__ __forceinline__ int floor_log2_p1(int64_t x)   // floor(log2(x + 1)),
     return 63 - __clzll((unsigned long long)(x + 1));
 }
 
+__device__ __forceinline__ bool graph_ok(const BatchArgs &a, int64_t g, int64_t &m, int64_t &n)
+{
+    const int64_t e0 = a.eoff[g], e1 = a.eoff[g + 1], v0 = a.voff[g], v1 = a.voff[g + 1];
+    m = e1 - e0;
+    n = v1 - v0;
+    return e0 >= 0 && v0 >= 0 && m >= 0 && n >= 0 && e1 <= a.total_m && v1 <= a.total_n &&
+           m <= a.max_m && n <= a.max_n && n <= (int64_t)kTeam * kKcap && !(n == 0 && m > 0);
+}
+
 // One block of 1024 threads: validate the offsets, bucket the graphs, write
-// the processing order and the work header, reset the ticket.
+// the processing order and the work header, reset the tickets, and tabulate
+// the tiles of the large graphs (exclusive prefixes over order[0 .. L)).
 __global__ void __launch_bounds__(1024) k_batch_plan(BatchArgs a)
 {
     __shared__ uint32_t hist[128], cur[128];
+    __shared__ typename BlockScan<1024>::Smem sm;
+    __shared__ uint32_t carry[4];
     for (int i = threadIdx.x; i < 128; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     for (int64_t g = threadIdx.x; g < a.G; g += blockDim.x) {
-        const int64_t e0 = a.eoff[g], e1 = a.eoff[g + 1], v0 = a.voff[g], v1 = a.voff[g + 1];
-        const int64_t m = e1 - e0, n = v1 - v0;
-        const bool ok = e0 >= 0 && v0 >= 0 && m >= 0 && n >= 0 && e1 <= a.total_m &&
-                        v1 <= a.total_n && m <= a.max_m && n <= a.max_n &&
-                        n <= (int64_t)kTeam * kKcap && !(n == 0 && m > 0);
-        if (!ok) { raise_status(a.status, BOBA_ERR_INVALID_ARG); continue; }
+        int64_t m, n;
+        if (!graph_ok(a, g, m, n)) { raise_status(a.status, BOBA_ERR_INVALID_ARG); continue; }
         if (n == 0) continue;
-        const int lg = floor_log2_p1(m) & 63;
-        const int b = (n > kKcap ? 0 : 64) + (63 - lg);
+        const int b = (n > a.large_threshold ? 0 : 64) + (63 - (floor_log2_p1(m) & 63));
         atomicAdd(&hist[b], 1u);
     }
     __syncthreads();
@@ -86,18 +122,41 @@ __global__ void __launch_bounds__(1024) k_batch_plan(BatchArgs a)
         a.hdr[kHdrValid] = s;
         a.hdr[kHdrItems] = large + (s - large + kTeam - 1) / kTeam;
         a.hdr[kHdrTicket] = 0;
+        a.hdr[kHdrScanTicket] = 0;
+        a.hdr[kHdrEmitTicket] = 0;
+        for (int k = 0; k < 4; ++k) carry[k] = 0;
     }
     __syncthreads();
     for (int64_t g = threadIdx.x; g < a.G; g += blockDim.x) {
-        const int64_t e0 = a.eoff[g], e1 = a.eoff[g + 1], v0 = a.voff[g], v1 = a.voff[g + 1];
-        const int64_t m = e1 - e0, n = v1 - v0;
-        const bool ok = e0 >= 0 && v0 >= 0 && m >= 0 && n >= 0 && e1 <= a.total_m &&
-                        v1 <= a.total_n && m <= a.max_m && n <= a.max_n &&
-                        n <= (int64_t)kTeam * kKcap && !(n == 0 && m > 0);
-        if (!ok || n == 0) continue;
-        const int lg = floor_log2_p1(m) & 63;
-        const int b = (n > kKcap ? 0 : 64) + (63 - lg);
+        int64_t m, n;
+        if (!graph_ok(a, g, m, n) || n == 0) continue;
+        const int b = (n > a.large_threshold ? 0 : 64) + (63 - (floor_log2_p1(m) & 63));
         a.order[atomicAdd(&cur[b], 1u)] = (uint32_t)g;
+    }
+    __syncthreads();
+    if (a.lg_pc == nullptr) return;
+    const uint32_t L = a.hdr[kHdrLarge];
+    for (uint32_t base = 0; base <= L; base += blockDim.x) {
+        const uint32_t j = base + threadIdx.x;
+        uint32_t c[4] = {0, 0, 0, 0};
+        if (j < L) {
+            const uint32_t g = a.order[j];
+            const int64_t m = a.eoff[g + 1] - a.eoff[g], n = a.voff[g + 1] - a.voff[g];
+            c[0] = (uint32_t)cdiv(2 * m, kPosChunk);
+            c[1] = (uint32_t)cdiv(n, kVtxTile);
+            const int64_t words = cdiv(2 * m, 32) > 0 ? cdiv(2 * m, 32) : 1;
+            c[2] = (uint32_t)cdiv(words, kWordTile);
+            c[3] = (uint32_t)cdiv(m, kEdgeChunk);
+        }
+        uint32_t *tabs[4] = {a.lg_pc, a.lg_vt, a.lg_wt, a.lg_ec};
+        for (int k = 0; k < 4; ++k) {
+            uint32_t tot;
+            const uint32_t ex = BlockScan<1024>::exclusive(c[k], &tot, sm);
+            if (j <= L) tabs[k][j] = carry[k] + ex;
+            __syncthreads();
+            if (threadIdx.x == 0) carry[k] += tot;
+            __syncthreads();
+        }
     }
 }
 
@@ -111,10 +170,10 @@ struct TeamSmem {
 };
 
 template <int T>
-__device__ __forceinline__ void team_sync(cg::cluster_group &cl)
+__device__ __forceinline__ void team_sync(cg::cluster_group *cl)
 {
     if constexpr (T == 1) __syncthreads();
-    else cl.sync();
+    else cl->sync();
 }
 
 template <int T>
@@ -128,7 +187,7 @@ __device__ __forceinline__ uint32_t *key_ptr(uint32_t *s_keys, TeamSmem &ts, uin
 // are grid CTAs cta0 .. cta0+T-1 (their scratch regions).
 template <int T>
 __device__ void process_graph(const BatchArgs &a, uint32_t g, int t, int64_t cta0,
-                              cg::cluster_group &cl, uint32_t *s_keys, TeamSmem &ts)
+                              cg::cluster_group *cl, uint32_t *s_keys, TeamSmem &ts)
 {
     const int tid = threadIdx.x;
     const int64_t E0 = a.eoff[g], m = a.eoff[g + 1] - E0;
@@ -144,7 +203,7 @@ __device__ void process_graph(const BatchArgs &a, uint32_t g, int t, int64_t cta
     uint32_t *const my_grp = my_bm + a.wmax;
 
     if constexpr (T > 1) {
-        if (tid < T) ts.kp[tid] = cl.map_shared_rank(s_keys, tid);
+        if (tid < T) ts.kp[tid] = cl->map_shared_rank(s_keys, tid);
     }
     // 1. keys = SENT, clear this member's bitmap slice
     for (int64_t i = tid; i < myn; i += kBB) s_keys[i] = kSent;
@@ -232,8 +291,8 @@ __device__ void process_graph(const BatchArgs &a, uint32_t g, int t, int64_t cta
             uint32_t tr, ir;
             if constexpr (T == 1) { tr = ts.xtot; ir = ts.xiso; }
             else {
-                tr = *cl.map_shared_rank(&ts.xtot, r);
-                ir = *cl.map_shared_rank(&ts.xiso, r);
+                tr = *cl->map_shared_rank(&ts.xtot, r);
+                ir = *cl->map_shared_rank(&ts.xiso, r);
             }
             ts.base[r] = K;
             K += tr;
@@ -339,37 +398,307 @@ __global__ void __cluster_dims__(kTeam, 1, 1) __launch_bounds__(kBB, 1) k_batch(
         if (item >= n_items) break;
         const uint32_t n_large = a.hdr[kHdrLarge];
         if (item < n_large) {
-            process_graph<kTeam>(a, a.order[item], rank, cluster_cta0, cl, s_keys, ts);
+            process_graph<kTeam>(a, a.order[item], rank, cluster_cta0, &cl, s_keys, ts);
         } else {
             const uint32_t idx = n_large + (item - n_large) * kTeam + (uint32_t)rank;
             if (idx < a.hdr[kHdrValid])
-                process_graph<1>(a, a.order[idx], 0, (int64_t)blockIdx.x, cl, s_keys, ts);
+                process_graph<1>(a, a.order[idx], 0, (int64_t)blockIdx.x, nullptr, s_keys, ts);
         }
     }
 }
 
+// Split mode, small graphs: one CTA per graph, persistent, no clusters.
+__global__ void __launch_bounds__(kBB, 1) k_batch_small(BatchArgs a)
+{
+    extern __shared__ uint32_t s_keys[];
+    __shared__ TeamSmem ts;
+    const uint32_t n_large = a.hdr[kHdrLarge], n_valid = a.hdr[kHdrValid];
+    while (true) {
+        if (threadIdx.x == 0) ts.item = atomicAdd(&a.hdr[kHdrTicket], 1u);
+        __syncthreads();
+        const uint32_t idx = n_large + ts.item;
+        __syncthreads();
+        if (idx >= n_valid) break;
+        process_graph<1>(a, a.order[idx], 0, (int64_t)blockIdx.x, nullptr, s_keys, ts);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Split mode, large graphs: all of them together, phase by phase.
+// ---------------------------------------------------------------------------
+
+// Largest j in [0, L) with tab[j] <= x (tab[0] = 0, tab[L] = total, x < total).
+__device__ __forceinline__ uint32_t find_graph(const uint32_t *__restrict__ tab, uint32_t L, uint32_t x)
+{
+    uint32_t lo = 0, hi = L;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(tab + mid) <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+struct LargeItem {
+    uint32_t j;              // index among the large graphs
+    int64_t E0, m, V0, n;
+    uint32_t local;          // chunk / tile index within the graph
+};
+
+__device__ __forceinline__ void block_find(const BatchArgs &a, const uint32_t *tab, uint32_t x,
+                                           LargeItem &it, LargeItem &s_it)
+{
+    if (threadIdx.x == 0) {
+        const uint32_t L = a.hdr[kHdrLarge];
+        s_it.j = find_graph(tab, L, x);
+        const uint32_t g = a.order[s_it.j];
+        s_it.E0 = a.eoff[g];
+        s_it.m = a.eoff[g + 1] - s_it.E0;
+        s_it.V0 = a.voff[g];
+        s_it.n = a.voff[g + 1] - s_it.V0;
+        s_it.local = x - tab[s_it.j];
+    }
+    __syncthreads();
+    it = s_it;
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kLB) k_bl_init(BatchArgs a)
+{
+    __shared__ LargeItem s_it;
+    const uint32_t L = a.hdr[kHdrLarge];
+    const uint32_t vt = a.lg_vt[L], wt = a.lg_wt[L];
+    // keys of every large graph = SENT (padding too), clear bitmaps and scan state
+    const int64_t stride = (int64_t)gridDim.x * kLB;
+    const uint4 sent = make_uint4(kSent, kSent, kSent, kSent), z = make_uint4(0, 0, 0, 0);
+    for (int64_t i = (int64_t)blockIdx.x * kLB + threadIdx.x; i < (int64_t)vt * kVtxTile / 4; i += stride)
+        reinterpret_cast<uint4 *>(a.kl)[i] = sent;
+    for (int64_t i = (int64_t)blockIdx.x * kLB + threadIdx.x; i < (int64_t)wt * kWordTile / 4; i += stride)
+        reinterpret_cast<uint4 *>(a.lbm)[i] = z;
+    for (int64_t i = (int64_t)blockIdx.x * kLB + threadIdx.x; i < wt; i += stride) a.lts_scan[i] = 0;
+    for (int64_t i = (int64_t)blockIdx.x * kLB + threadIdx.x; i < vt; i += stride) a.lts_emit[i] = 0;
+    (void)s_it;
+}
+
+__global__ void __launch_bounds__(kLB) k_bl_first(BatchArgs a)
+{
+    __shared__ LargeItem s_it;
+    const uint32_t L = a.hdr[kHdrLarge];
+    const uint32_t total = a.lg_pc[L];
+    constexpr int U = kPosChunk / kLB;
+    for (uint32_t c = blockIdx.x; c < total; c += gridDim.x) {
+        LargeItem it;
+        block_find(a, a.lg_pc, c, it, s_it);
+        const uint32_t nn = (uint32_t)it.n;
+        uint32_t *key = a.kl + (size_t)a.lg_vt[it.j] * kVtxTile;
+        const int64_t p0 = (int64_t)it.local * kPosChunk;
+        const int64_t p1 = min(p0 + (int64_t)kPosChunk, 2 * it.m);
+        int32_t v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = p0 + u * kLB + threadIdx.x;
+            v[u] = -1;
+            if (i < p1) v[u] = i < it.m ? __ldcs(a.src + it.E0 + i) : __ldcs(a.dst + it.E0 + (i - it.m));
+        }
+        uint32_t cur[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) cur[u] = (uint32_t)v[u] < nn ? key[v[u]] : 0u;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = p0 + u * kLB + threadIdx.x;
+            if (i >= p1) continue;
+            if ((uint32_t)v[u] >= nn) raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
+            else if (cur[u] > (uint32_t)i) atomicMin(&key[v[u]], (uint32_t)i);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kLB) k_bl_mark(BatchArgs a)
+{
+    __shared__ LargeItem s_it;
+    const uint32_t L = a.hdr[kHdrLarge];
+    const uint32_t total = a.lg_vt[L];
+    for (uint32_t c = blockIdx.x; c < total; c += gridDim.x) {
+        LargeItem it;
+        block_find(a, a.lg_vt, c, it, s_it);
+        const uint32_t *key = a.kl + (size_t)a.lg_vt[it.j] * kVtxTile;
+        uint32_t *bm = a.lbm + (size_t)a.lg_wt[it.j] * kWordTile;
+        const int64_t v0 = (int64_t)it.local * kVtxTile + 4 * threadIdx.x;
+        const uint4 k4 = *reinterpret_cast<const uint4 *>(key + v0);
+        const uint32_t kk[4] = {k4.x, k4.y, k4.z, k4.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (v0 + q < it.n && kk[q] != kSent) atomicOr(&bm[kk[q] >> 5], 1u << (kk[q] & 31u));
+    }
+}
+
+__global__ void __launch_bounds__(kLB) k_bl_scan(BatchArgs a)
+{
+    __shared__ LargeItem s_it;
+    __shared__ typename BlockScan<kLB>::Smem sm;
+    __shared__ uint32_t s_tile;
+    __shared__ uint64_t s_pre;
+    const uint32_t L = a.hdr[kHdrLarge];
+    const uint32_t total = a.lg_wt[L];
+    while (true) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&a.hdr[kHdrScanTicket], 1u);
+        __syncthreads();
+        const uint32_t t = s_tile;
+        __syncthreads();
+        if (t >= total) break;
+        LargeItem it;
+        block_find(a, a.lg_wt, t, it, s_it);
+        const size_t w0 = (size_t)t * kWordTile + 8 * threadIdx.x;
+        const uint4 x0 = __ldcg(reinterpret_cast<const uint4 *>(a.lbm + w0));
+        const uint4 x1 = __ldcg(reinterpret_cast<const uint4 *>(a.lbm + w0) + 1);
+        const uint32_t c = __popc(x0.x) + __popc(x0.y) + __popc(x0.z) + __popc(x0.w) +
+                           __popc(x1.x) + __popc(x1.y) + __popc(x1.z) + __popc(x1.w);
+        uint32_t tot;
+        const uint32_t ex = BlockScan<kLB>::exclusive(c, &tot, sm);
+        if (threadIdx.x < 32) {
+            const uint64_t p = lookback_exclusive(a.lts_scan, t, tot, a.status, it.local == 0);
+            if (threadIdx.x == 0) s_pre = p;
+        }
+        __syncthreads();
+        a.lgrp[w0 >> 3] = (uint32_t)s_pre + ex;
+        if (threadIdx.x == 0 && t + 1 == a.lg_wt[it.j + 1]) a.lg_tot[it.j] = (uint32_t)s_pre + tot;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kLB) k_bl_emit(BatchArgs a)
+{
+    __shared__ LargeItem s_it;
+    __shared__ typename BlockScan<kLB>::Smem sm;
+    __shared__ uint32_t s_tile;
+    __shared__ uint64_t s_pre;
+    const uint32_t L = a.hdr[kHdrLarge];
+    const uint32_t total = a.lg_vt[L];
+    while (true) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&a.hdr[kHdrEmitTicket], 1u);
+        __syncthreads();
+        const uint32_t t = s_tile;
+        __syncthreads();
+        if (t >= total) break;
+        LargeItem it;
+        block_find(a, a.lg_vt, t, it, s_it);
+        uint32_t *key = a.kl + (size_t)a.lg_vt[it.j] * kVtxTile;
+        const size_t wbase = (size_t)a.lg_wt[it.j] * kWordTile;
+        const int64_t v0 = (int64_t)it.local * kVtxTile + 4 * threadIdx.x;
+        const uint4 k4 = *reinterpret_cast<const uint4 *>(key + v0);
+        const uint32_t kk[4] = {k4.x, k4.y, k4.z, k4.w};
+        uint32_t c = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) c += (v0 + q < it.n && kk[q] == kSent) ? 1u : 0u;
+        uint32_t tot;
+        const uint32_t ex = BlockScan<kLB>::exclusive(c, &tot, sm);
+        if (threadIdx.x < 32) {
+            const uint64_t p = lookback_exclusive(a.lts_emit, t, tot, a.status, it.local == 0);
+            if (threadIdx.x == 0) s_pre = p;
+        }
+        __syncthreads();
+        const uint32_t K = __ldcg(a.lg_tot + it.j);
+        uint32_t next_iso = K + (uint32_t)s_pre + ex;
+        uint32_t lab[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            lab[q] = kSent;
+            if (v0 + q >= it.n) continue;
+            if (kk[q] == kSent) {
+                lab[q] = next_iso++;
+            } else {
+                const uint32_t k = kk[q];
+                const size_t gidx = (wbase >> 3) + (k >> 8);
+                const uint4 *gw = reinterpret_cast<const uint4 *>(a.lbm + (gidx << 3));
+                const uint4 q0 = __ldcg(gw), q1 = __ldcg(gw + 1);
+                const uint32_t ws[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+                const uint32_t wi = (k >> 5) & 7u;
+                uint32_t r = __ldcg(a.lgrp + gidx);      // prefixes restart at each graph
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    if ((uint32_t)i < wi) r += __popc(ws[i]);
+                    else if ((uint32_t)i == wi) r += __popc(ws[i] & ((1u << (k & 31u)) - 1u));
+                }
+                lab[q] = r;
+            }
+            if (lab[q] < (uint32_t)it.n) a.perm[it.V0 + lab[q]] = (int32_t)(v0 + q);
+            else raise_status(a.status, BOBA_ERR_TIMEOUT);
+        }
+        *reinterpret_cast<uint4 *>(key + v0) = make_uint4(lab[0], lab[1], lab[2], lab[3]);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kLB) k_bl_relabel(BatchArgs a)
+{
+    __shared__ LargeItem s_it;
+    const uint32_t L = a.hdr[kHdrLarge];
+    const uint32_t total = a.lg_ec[L];
+    constexpr int U = kEdgeChunk / kLB;
+    for (uint32_t c = blockIdx.x; c < total; c += gridDim.x) {
+        LargeItem it;
+        block_find(a, a.lg_ec, c, it, s_it);
+        const uint32_t nn = (uint32_t)it.n;
+        const uint32_t *lab = a.kl + (size_t)a.lg_vt[it.j] * kVtxTile;
+        const int64_t e0 = (int64_t)it.local * kEdgeChunk;
+        const int64_t e1 = min(e0 + (int64_t)kEdgeChunk, it.m);
+        int32_t s[U], d[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t e = e0 + u * kLB + threadIdx.x;
+            s[u] = d[u] = -1;
+            if (e < e1) {
+                s[u] = __ldcs(a.src + it.E0 + e);
+                d[u] = __ldcs(a.dst + it.E0 + e);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            s[u] = (uint32_t)s[u] < nn ? (int32_t)__ldg(lab + s[u]) : -1;
+            d[u] = (uint32_t)d[u] < nn ? (int32_t)__ldg(lab + d[u]) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t e = e0 + u * kLB + threadIdx.x;
+            if (e >= e1) continue;
+            if (s[u] < 0 || d[u] < 0) raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
+            __stcs(a.so + it.E0 + e, s[u]);
+            __stcs(a.dout + it.E0 + e, d[u]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
 struct BatchDevice {
     bool ready = false;
-    int grid_ctas = 0;
+    int grid_cluster = 0;    // CTAs of the persistent cluster launch
+    int grid_small = 0;      // CTAs of the persistent non-cluster launch
+    int sms = 0;
 };
 std::mutex g_bmu;
 BatchDevice g_bdev[64];
+int g_mode_override = -1;    // set by the autotuner API; -1 = default
 
-// Grid of the persistent launch on the current device: every cluster that fits.
-int batch_grid_ctas()
+const BatchDevice *batch_device()
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
         (void)cudaGetLastError();
-        return 0;
+        return nullptr;
     }
     std::lock_guard<std::mutex> lk(g_bmu);
     BatchDevice &d = g_bdev[dev];
     if (!d.ready) {
         if (cudaFuncSetAttribute((const void *)k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kDynSmem) != cudaSuccess) {
+                                 (int)kDynSmem) != cudaSuccess ||
+            cudaFuncSetAttribute((const void *)k_batch_small,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kDynSmem) != cudaSuccess ||
+            cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
             (void)cudaGetLastError();
-            return 0;
+            return nullptr;
         }
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(kTeam, 1, 1);
@@ -379,30 +708,56 @@ int batch_grid_ctas()
         if (cudaOccupancyMaxActiveClusters(&clusters, (const void *)k_batch, &cfg) != cudaSuccess ||
             clusters < 1) {
             (void)cudaGetLastError();
-            return 0;
+            return nullptr;
         }
-        d.grid_ctas = clusters * kTeam;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_batch_small, kBB,
+                                                          kDynSmem) != cudaSuccess || per_sm < 1) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        d.grid_cluster = clusters * kTeam;
+        d.grid_small = d.sms * per_sm;
         d.ready = true;
     }
-    return d.grid_ctas;
+    return &d;
+}
+
+int batch_mode()
+{
+    if (g_mode_override >= 0) return g_mode_override;
+    const char *e = getenv("BOBA_BATCH_MODE");
+    if (e && strcmp(e, "cluster") == 0) return kBatchCluster;
+    return kBatchSplit;
 }
 
 struct BatchLayout {
-    int64_t wmax, region_words;
-    size_t hdr, order, scratch, total;
+    int64_t wmax, region_words, regions, lvt_cap, lwt_cap;
+    size_t hdr, order, scratch, tabs, kl, lbm, lgrp, lts_scan, lts_emit, total;
 };
 
-bool batch_layout(int64_t G, int64_t max_m, int64_t max_n, int grid_ctas, BatchLayout &L)
+bool batch_layout(int64_t G, int64_t max_m, int64_t max_n, int64_t total_m, int64_t total_n,
+                  const BatchDevice *d, BatchLayout &L)
 {
-    if (G < 0 || max_m < 0 || max_n < 0 || max_m > kMaxSize || max_n > kMaxSize || grid_ctas < 1)
+    if (G < 0 || max_m < 0 || max_n < 0 || total_m < 0 || total_n < 0 || max_m > kMaxSize ||
+        max_n > kMaxSize || d == nullptr)
         return false;
     L.wmax = (int64_t)align_up((size_t)(cdiv(2 * max_m, 32) > 0 ? cdiv(2 * max_m, 32) : 1),
                                (size_t)8 * kTeam);
     L.region_words = L.wmax + L.wmax / 8;
+    L.regions = d->grid_cluster > d->grid_small ? d->grid_cluster : d->grid_small;
+    L.lvt_cap = total_n / kVtxTile + G + 1;
+    L.lwt_cap = (2 * total_m / 32) / kWordTile + G + 1;
     Carve c;
     L.hdr = c.take(64);
     L.order = c.take((size_t)(G > 0 ? G : 1) * 4);
-    L.scratch = c.take((size_t)grid_ctas * L.region_words * 4);
+    L.scratch = c.take((size_t)L.regions * L.region_words * 4);
+    L.tabs = c.take((size_t)5 * (G + 1) * 4);
+    L.kl = c.take((size_t)L.lvt_cap * kVtxTile * 4);
+    L.lbm = c.take((size_t)L.lwt_cap * kWordTile * 4);
+    L.lgrp = c.take((size_t)L.lwt_cap * kWordTile / 8 * 4);
+    L.lts_scan = c.take((size_t)L.lwt_cap * 8);
+    L.lts_emit = c.take((size_t)L.lvt_cap * 8);
     L.total = c.off;
     return true;
 }
@@ -412,10 +767,11 @@ bool batch_layout(int64_t G, int64_t max_m, int64_t max_n, int grid_ctas, BatchL
 
 using namespace boba;
 
-extern "C" size_t boba_reorder_batched_workspace_bytes(int64_t G, int64_t max_m, int64_t max_n)
+extern "C" size_t boba_reorder_batched_workspace_bytes(int64_t G, int64_t max_m, int64_t max_n,
+                                                       int64_t total_m, int64_t total_n)
 {
     BatchLayout L;
-    if (!batch_layout(G, max_m, max_n, batch_grid_ctas(), L)) return 0;
+    if (!batch_layout(G, max_m, max_n, total_m, total_n, batch_device(), L)) return 0;
     return L.total;
 }
 
@@ -434,16 +790,18 @@ extern "C" boba_status_t boba_reorder_batched(const int32_t *src, const int32_t 
     if (total_m > 0 && (src == nullptr || dst == nullptr || src_out == nullptr || dst_out == nullptr))
         return BOBA_ERR_INVALID_ARG;
     if (total_n > 0 && perm_out == nullptr) return BOBA_ERR_INVALID_ARG;
-    const int grid = batch_grid_ctas();
-    if (grid < 1) return BOBA_ERR_CUDA;
+    const BatchDevice *bd = batch_device();
+    if (!bd) return BOBA_ERR_CUDA;
     BatchLayout L;
-    if (!batch_layout(G, max_m, max_n, grid, L)) return BOBA_ERR_INVALID_ARG;
+    if (!batch_layout(G, max_m, max_n, total_m, total_n, bd, L)) return BOBA_ERR_INVALID_ARG;
     if (ws == nullptr || ws_bytes < L.total || !aligned256(ws)) return BOBA_ERR_WORKSPACE;
     const DeviceInfo *dev = device_info();
     if (!dev) return BOBA_ERR_CUDA;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    const int mode = batch_mode();
     char *b = static_cast<char *>(ws);
     BatchArgs a;
+    memset(&a, 0, sizeof(a));
     a.src = src;
     a.dst = dst;
     a.eoff = edge_off;
@@ -462,8 +820,40 @@ extern "C" boba_status_t boba_reorder_batched(const int32_t *src, const int32_t 
     a.region_words = L.region_words;
     a.wmax = L.wmax;
     a.status = dev->status;
+    a.large_threshold = kKcap;
+    if (mode == kBatchSplit) {
+        uint32_t *tabs = reinterpret_cast<uint32_t *>(b + L.tabs);
+        a.lg_pc = tabs;
+        a.lg_vt = tabs + (G + 1);
+        a.lg_wt = tabs + 2 * (G + 1);
+        a.lg_ec = tabs + 3 * (G + 1);
+        a.lg_tot = tabs + 4 * (G + 1);
+        a.kl = reinterpret_cast<uint32_t *>(b + L.kl);
+        a.lbm = reinterpret_cast<uint32_t *>(b + L.lbm);
+        a.lgrp = reinterpret_cast<uint32_t *>(b + L.lgrp);
+        a.lts_scan = reinterpret_cast<uint64_t *>(b + L.lts_scan);
+        a.lts_emit = reinterpret_cast<uint64_t *>(b + L.lts_emit);
+        a.lts_scan_cap = L.lwt_cap;
+        a.lts_emit_cap = L.lvt_cap;
+    }
     BOBA_TIMED("batch.plan", stream, k_batch_plan<<<1, 1024, 0, stream>>>(a));
-    BOBA_TIMED("batch.reorder", stream, k_batch<<<grid, kBB, kDynSmem, stream>>>(a));
+    if (mode == kBatchCluster) {
+        BOBA_TIMED("batch.reorder", stream,
+                   k_batch<<<bd->grid_cluster, kBB, kDynSmem, stream>>>(a));
+    } else {
+        const int gl = bd->sms * 8;
+        BOBA_TIMED("batch.small", stream,
+                   k_batch_small<<<bd->grid_small, kBB, kDynSmem, stream>>>(a));
+        BOBA_TIMED("batch.large", stream, k_bl_init<<<gl, kLB, 0, stream>>>(a));
+        BOBA_TIMED("batch.large", stream, k_bl_first<<<gl, kLB, 0, stream>>>(a));
+        BOBA_TIMED("batch.large", stream, k_bl_mark<<<gl, kLB, 0, stream>>>(a));
+        BOBA_TIMED("batch.large", stream, k_bl_scan<<<gl, kLB, 0, stream>>>(a));
+        BOBA_TIMED("batch.large", stream, k_bl_emit<<<gl, kLB, 0, stream>>>(a));
+        BOBA_TIMED("batch.large", stream, k_bl_relabel<<<gl, kLB, 0, stream>>>(a));
+    }
     BOBA_LAUNCH_CHECK();
     return BOBA_OK;
 }
+
+// Selects the batched mode explicitly (autotuner hook): 0 cluster, 1 split, -1 default.
+extern "C" void boba_batched_set_mode(int mode) { g_mode_override = (mode == 0 || mode == 1) ? mode : -1; }

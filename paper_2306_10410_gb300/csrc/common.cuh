@@ -134,13 +134,15 @@ struct OpMax {
 // Called by all 32 lanes of ONE warp.  Returns the exclusive prefix of tile
 // `tile` under Op (same value in every lane; the identity, 0, for tile 0) and
 // publishes its inclusive prefix.  Values must fit in 62 bits.
+// `seg_first` marks the first tile of a segment: it publishes its inclusive
+// prefix at once, and no look-back walks past it (segmented scans).
 template <class Op = OpSum>
 __device__ __forceinline__ uint64_t lookback_exclusive(uint64_t *tstat, int64_t tile, uint64_t agg,
-                                                       uint32_t *status)
+                                                       uint32_t *status, bool seg_first = false)
 {
     const int lane = threadIdx.x & 31;
-    if (tile == 0) {
-        if (lane == 0) st_relaxed_u64(&tstat[0], kFlagPre | agg);
+    if (tile == 0 || seg_first) {
+        if (lane == 0) st_relaxed_u64(&tstat[tile], kFlagPre | agg);
         return 0;
     }
     if (lane == 0) st_relaxed_u64(&tstat[tile], kFlagAgg | agg);

@@ -17,7 +17,11 @@ TEAM_MAX = 8 * KCAP       # largest graph a cluster handles
 def boba():
     import paper_2306_10410_gb300 as b
     b.load()
-    return b
+    yield b
+    b.boba_batched_set_mode(-1)
+
+
+MODES = [pytest.param(0, id="cluster"), pytest.param(1, id="split")]
 
 
 def pack(graphs):
@@ -48,7 +52,9 @@ def check_against_oracle(graphs, perm, so, do, eo, vo, which=None):
         np.testing.assert_array_equal(do[eo[g]:eo[g + 1]], odo, err_msg=f"graph {g}")
 
 
-def test_mixed_small_batch(boba):
+@pytest.mark.parametrize("mode", MODES)
+def test_mixed_small_batch(boba, mode):
+    boba.boba_batched_set_mode(mode)
     rng = np.random.default_rng(0)
     graphs = []
     for g in range(60):
@@ -70,8 +76,11 @@ def test_mixed_small_batch(boba):
     check_against_oracle(graphs, perm, so, do, eo, vo)
 
 
-def test_team_path_large_graphs(boba):
-    """Graphs above one CTA's capacity go to an 8-CTA cluster (distributed shared memory)."""
+@pytest.mark.parametrize("mode", MODES)
+def test_large_graphs(boba, mode):
+    """Graphs above one CTA's capacity: an 8-CTA cluster (distributed shared memory)
+    or the phase-batched global-memory path."""
+    boba.boba_batched_set_mode(mode)
     graphs = []
     for n, m, seed in ((KCAP + 1, 200_000, 1), (150_000, 2_400_000, 2), (TEAM_MAX, 3_000_000, 3),
                        (KCAP, 500_000, 4), (300, 9000, 5)):
@@ -83,9 +92,11 @@ def test_team_path_large_graphs(boba):
     check_against_oracle(graphs, perm, so, do, eo, vo)
 
 
-def test_rmat_batch_equals_single_graph_entry(boba):
+@pytest.mark.parametrize("mode", MODES)
+def test_rmat_batch_equals_single_graph_entry(boba, mode):
     """A batch drawn like the evaluation's (log-uniform sizes, edge factor 4..32),
     smaller: batched output == boba_reorder per graph == oracle (on a sample)."""
+    boba.boba_batched_set_mode(mode)
     src, dst, eo, vo = synth.rmat_batch(300, seed=17, log2_lo=8, log2_hi=17)
     perm, so, do = run_batched(boba, src, dst, eo, vo)
     s_d, d_d = torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda()
@@ -101,7 +112,9 @@ def test_rmat_batch_equals_single_graph_entry(boba):
     check_against_oracle(graphs, perm, so, do, eo, vo, which=range(0, 300, 17))
 
 
-def test_bad_offsets_are_skipped_and_reported(boba):
+@pytest.mark.parametrize("mode", MODES)
+def test_bad_offsets_are_skipped_and_reported(boba, mode):
+    boba.boba_batched_set_mode(mode)
     rng = np.random.default_rng(5)
     graphs = [(rng.integers(0, 100, 500).astype(np.int32), rng.integers(0, 100, 500).astype(np.int32),
                100) for _ in range(3)]
@@ -124,7 +137,7 @@ def test_size_limits(boba):
     z = torch.zeros(8, dtype=torch.int64, device="cuda")
     i = torch.zeros(8, dtype=torch.int32, device="cuda")
     assert boba.boba_reorder_batched(i, i, z, z, 1, 4, TEAM_MAX + 1, 4, 4, i, i, i, None, 0) == 3
-    assert boba.boba_reorder_batched_workspace_bytes(4096, 1 << 23, TEAM_MAX) > 0
+    assert boba.boba_reorder_batched_workspace_bytes(4096, 1 << 23, TEAM_MAX, 1 << 31, 1 << 28) > 0
 
 
 @pytest.mark.slow
@@ -135,9 +148,14 @@ def test_full_batch_4096_graphs(boba):
     G = 4096
     src, dst, eo, vo = synth.rmat_batch(G, seed=synth.SEED_BASE + 3)
     s_d, d_d = torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda()
-    perm, so, do = boba.reorder_batched(s_d, d_d, torch.from_numpy(eo).cuda(),
-                                        torch.from_numpy(vo).cuda())
+    eo_d, vo_d = torch.from_numpy(eo).cuda(), torch.from_numpy(vo).cuda()
+    boba.boba_batched_set_mode(0)
+    perm0, so0, do0 = boba.reorder_batched(s_d, d_d, eo_d, vo_d)
+    boba.boba_batched_set_mode(1)
+    perm, so, do = boba.reorder_batched(s_d, d_d, eo_d, vo_d)
     boba.stream_status()
+    assert torch.equal(perm0, perm) and torch.equal(so0, so) and torch.equal(do0, do)
+    del perm0, so0, do0
     for g in range(G):
         n = int(vo[g + 1] - vo[g])
         p1, s1, d1 = boba.reorder(s_d[eo[g]:eo[g + 1]], d_d[eo[g]:eo[g + 1]], n)
