@@ -153,9 +153,10 @@ boba_status_t boba_reorder_static(const int32_t *src, const int32_t *dst, int64_
  *   edge_off     int64[G+1], non-decreasing, edge_off[G] <= total_m   (device)
  *   vert_off     int64[G+1], non-decreasing, vert_off[G] <= total_n   (device)
  *   G            number of graphs, >= 0
- *   max_m, max_n upper bounds on any one graph's edges (<= 2^31 - 1) and
- *                vertices (<= 442,368 = 8 x 55,296: a graph's key array must
- *                fit in the shared memory of one 8-CTA cluster)
+ *   max_m, max_n upper bounds on any one graph's edges and vertices
+ *                (<= 2^31 - 1; in the cluster mode of boba_batched_set_mode
+ *                also max_n <= 442,368 = 8 x 55,296, so that a graph's key
+ *                array fits in the shared memory of one 8-CTA cluster)
  *   total_m, total_n  sizes of the packed arrays (host-known)
  *   perm_out     int32[total_n], packed by vert_off, local labels    (device)
  *   src_out, dst_out int32[total_m], packed by edge_off, local labels (device)
@@ -191,6 +192,62 @@ size_t boba_reorder_batched_workspace_bytes(int64_t G, int64_t max_m, int64_t ma
  * "cluster" or "split").  Both give identical results.  Process-wide; host only.
  */
 void boba_batched_set_mode(int mode);
+
+/* ------------------------------------------------------------------------
+ * Serving: reorder + CSR + SpMV requests under an HBM budget
+ * ------------------------------------------------------------------------ */
+
+typedef struct boba_server boba_server_t;
+
+/*
+ * boba_server_create -- a serving runtime on the current device.  Requests
+ * are reordered with BOBA, converted to CSR (boba_coo_to_csr) and multiplied
+ * spmv_iters times (boba_spmv_csr, y = A x with the same x), the workflow the
+ * paper measures (Sec. 5.3).
+ *   hbm_budget_bytes  device memory for all resident requests: allocated once
+ *                     here (the only allocation of the server); requests are
+ *                     admitted in arrival order while their arrays fit in it
+ *   max_active        most requests on the device at once
+ *   n_streams         CUDA streams the requests are spread over
+ * Requests admitted together (a wave) are reordered by one batched launch;
+ * each then runs on its own stream.  A request's results do not depend on
+ * the other requests.  Returns NULL on invalid arguments or CUDA failure.
+ */
+boba_server_t *boba_server_create(size_t hbm_budget_bytes, int max_active, int spmv_iters,
+                                  int n_streams);
+
+/*
+ * boba_server_submit -- enqueue a request; returns its id (>= 0), -1 for
+ * invalid arguments, -2 if it could never fit in the budget.  HOST pointers:
+ * src, dst int32[m]; x float[n] (NULL: x is left uninitialised); outputs
+ * y float[n] and perm int32[n] (either may be NULL).  They must stay valid
+ * until the request is returned by boba_server_poll; pinned memory makes the
+ * copies asynchronous.
+ */
+int64_t boba_server_submit(boba_server_t *server, const int32_t *src, const int32_t *dst,
+                           int64_t m, int64_t n, const float *x, float *y, int32_t *perm);
+
+/*
+ * boba_server_poll -- up to cap completed requests since the last poll: ids,
+ * latency from submit to completion (ms), status (boba_status_t); returns the
+ * number written.  After a request is returned its outputs are complete.
+ */
+int boba_server_poll(boba_server_t *server, int64_t *ids, double *latency_ms, int *status,
+                     int cap);
+
+/* boba_server_drain -- blocks until every submitted request has completed. */
+boba_status_t boba_server_drain(boba_server_t *server);
+
+/*
+ * boba_server_stats -- out[0] p50 latency (ms), out[1] p99 latency (ms),
+ * out[2] throughput (Gedges/s over first arrival .. last completion),
+ * out[3] requests done, out[4] edges done, out[5] peak pool bytes in use,
+ * out[6] seconds spanned.  cap >= 7; returns 7.
+ */
+int boba_server_stats(boba_server_t *server, double *out, int cap);
+
+/* boba_server_destroy -- drains, stops the scheduler, frees the pool. */
+void boba_server_destroy(boba_server_t *server);
 
 /* ------------------------------------------------------------------------
  * Measurement path: COO -> CSR and SpMV (Alg. 3, Sec. 1.2.2)

@@ -45,6 +45,12 @@ SIGNATURES = {
     "boba_stream_status": (_ST, [_P]),
     "boba_status_string": (ctypes.c_char_p, [_ST]),
     "boba_version": (ctypes.c_char_p, []),
+    "boba_server_create": (_P, [_SZ, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "boba_server_submit": (_I64, [_P, _P, _P, _I64, _I64, _P, _P, _P]),
+    "boba_server_poll": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
+    "boba_server_drain": (_ST, [_P]),
+    "boba_server_stats": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "boba_server_destroy": (None, [_P]),
     "boba_timing_enable": (None, [ctypes.c_int]),
     "boba_timing_collect": (ctypes.c_int, []),
     "boba_timing_name": (ctypes.c_char_p, [ctypes.c_int]),

@@ -46,6 +46,7 @@ constexpr int kTeam = 8;                   // CTAs per cluster, team size for la
 constexpr int kKcap = 54 * 1024;           // vertices per CTA held in shared memory
 constexpr size_t kDynSmem = (size_t)kKcap * 4;
 constexpr int kU = 8;                      // stream loads in flight per thread
+constexpr int64_t kSmallMaxM = 1ll << 21;  // split mode: graphs with more edges go to the phase path
 constexpr int kHdrItems = 0, kHdrLarge = 1, kHdrTicket = 2, kHdrValid = 3, kHdrScanTicket = 4,
               kHdrEmitTicket = 5;
 
@@ -70,6 +71,8 @@ struct BatchArgs {
     int64_t wmax;
     uint32_t *status;
     int large_threshold;     // graphs with more vertices go to the team / phase path
+    int64_t small_max_m;     // ... and, in split mode, graphs with more edges
+    int64_t n_limit;         // largest graph the mode can take
     // phase-batched large-graph path (prefix tables over the large graphs, L+1 entries)
     uint32_t *lg_pc, *lg_vt, *lg_wt, *lg_ec, *lg_tot;
     uint32_t *kl;            // keys, then labels, of the large graphs (vertex-tile padded)
@@ -90,7 +93,7 @@ __device__ __forceinline__ bool graph_ok(const BatchArgs &a, int64_t g, int64_t 
     m = e1 - e0;
     n = v1 - v0;
     return e0 >= 0 && v0 >= 0 && m >= 0 && n >= 0 && e1 <= a.total_m && v1 <= a.total_n &&
-           m <= a.max_m && n <= a.max_n && n <= (int64_t)kTeam * kKcap && !(n == 0 && m > 0);
+           m <= a.max_m && n <= a.max_n && n <= a.n_limit && !(n == 0 && m > 0);
 }
 
 // One block of 1024 threads: validate the offsets, bucket the graphs, write
@@ -107,7 +110,8 @@ __global__ void __launch_bounds__(1024) k_batch_plan(BatchArgs a)
         int64_t m, n;
         if (!graph_ok(a, g, m, n)) { raise_status(a.status, BOBA_ERR_INVALID_ARG); continue; }
         if (n == 0) continue;
-        const int b = (n > a.large_threshold ? 0 : 64) + (63 - (floor_log2_p1(m) & 63));
+        const bool large = n > a.large_threshold || m > a.small_max_m;
+        const int b = (large ? 0 : 64) + (63 - (floor_log2_p1(m) & 63));
         atomicAdd(&hist[b], 1u);
     }
     __syncthreads();
@@ -130,7 +134,8 @@ __global__ void __launch_bounds__(1024) k_batch_plan(BatchArgs a)
     for (int64_t g = threadIdx.x; g < a.G; g += blockDim.x) {
         int64_t m, n;
         if (!graph_ok(a, g, m, n) || n == 0) continue;
-        const int b = (n > a.large_threshold ? 0 : 64) + (63 - (floor_log2_p1(m) & 63));
+        const bool large = n > a.large_threshold || m > a.small_max_m;
+        const int b = (large ? 0 : 64) + (63 - (floor_log2_p1(m) & 63));
         a.order[atomicAdd(&cur[b], 1u)] = (uint32_t)g;
     }
     __syncthreads();
@@ -464,7 +469,6 @@ __device__ __forceinline__ void block_find(const BatchArgs &a, const uint32_t *t
 
 __global__ void __launch_bounds__(kLB) k_bl_init(BatchArgs a)
 {
-    __shared__ LargeItem s_it;
     const uint32_t L = a.hdr[kHdrLarge];
     const uint32_t vt = a.lg_vt[L], wt = a.lg_wt[L];
     // keys of every large graph = SENT (padding too), clear bitmaps and scan state
@@ -476,7 +480,6 @@ __global__ void __launch_bounds__(kLB) k_bl_init(BatchArgs a)
         reinterpret_cast<uint4 *>(a.lbm)[i] = z;
     for (int64_t i = (int64_t)blockIdx.x * kLB + threadIdx.x; i < wt; i += stride) a.lts_scan[i] = 0;
     for (int64_t i = (int64_t)blockIdx.x * kLB + threadIdx.x; i < vt; i += stride) a.lts_emit[i] = 0;
-    (void)s_it;
 }
 
 __global__ void __launch_bounds__(kLB) k_bl_first(BatchArgs a)
@@ -737,12 +740,14 @@ struct BatchLayout {
 };
 
 bool batch_layout(int64_t G, int64_t max_m, int64_t max_n, int64_t total_m, int64_t total_n,
-                  const BatchDevice *d, BatchLayout &L)
+                  const BatchDevice *d, int mode, BatchLayout &L)
 {
     if (G < 0 || max_m < 0 || max_n < 0 || total_m < 0 || total_n < 0 || max_m > kMaxSize ||
         max_n > kMaxSize || d == nullptr)
         return false;
-    L.wmax = (int64_t)align_up((size_t)(cdiv(2 * max_m, 32) > 0 ? cdiv(2 * max_m, 32) : 1),
+    // per-CTA bitmap regions: in split mode only graphs up to kSmallMaxM edges use them
+    const int64_t region_m = mode == kBatchSplit ? (max_m < kSmallMaxM ? max_m : kSmallMaxM) : max_m;
+    L.wmax = (int64_t)align_up((size_t)(cdiv(2 * region_m, 32) > 0 ? cdiv(2 * region_m, 32) : 1),
                                (size_t)8 * kTeam);
     L.region_words = L.wmax + L.wmax / 8;
     L.regions = d->grid_cluster > d->grid_small ? d->grid_cluster : d->grid_small;
@@ -771,7 +776,7 @@ extern "C" size_t boba_reorder_batched_workspace_bytes(int64_t G, int64_t max_m,
                                                        int64_t total_m, int64_t total_n)
 {
     BatchLayout L;
-    if (!batch_layout(G, max_m, max_n, total_m, total_n, batch_device(), L)) return 0;
+    if (!batch_layout(G, max_m, max_n, total_m, total_n, batch_device(), batch_mode(), L)) return 0;
     return L.total;
 }
 
@@ -784,7 +789,8 @@ extern "C" boba_status_t boba_reorder_batched(const int32_t *src, const int32_t 
 {
     if (G < 0 || max_m < 0 || max_n < 0 || total_m < 0 || total_n < 0) return BOBA_ERR_INVALID_ARG;
     if (max_m > kMaxSize || max_n > kMaxSize) return BOBA_ERR_TOO_LARGE;
-    if (max_n > (int64_t)kTeam * kKcap) return BOBA_ERR_TOO_LARGE;
+    const int mode = batch_mode();
+    if (mode == kBatchCluster && max_n > (int64_t)kTeam * kKcap) return BOBA_ERR_TOO_LARGE;
     if (G == 0) return BOBA_OK;
     if (edge_off == nullptr || vert_off == nullptr) return BOBA_ERR_INVALID_ARG;
     if (total_m > 0 && (src == nullptr || dst == nullptr || src_out == nullptr || dst_out == nullptr))
@@ -793,12 +799,11 @@ extern "C" boba_status_t boba_reorder_batched(const int32_t *src, const int32_t 
     const BatchDevice *bd = batch_device();
     if (!bd) return BOBA_ERR_CUDA;
     BatchLayout L;
-    if (!batch_layout(G, max_m, max_n, total_m, total_n, bd, L)) return BOBA_ERR_INVALID_ARG;
+    if (!batch_layout(G, max_m, max_n, total_m, total_n, bd, mode, L)) return BOBA_ERR_INVALID_ARG;
     if (ws == nullptr || ws_bytes < L.total || !aligned256(ws)) return BOBA_ERR_WORKSPACE;
     const DeviceInfo *dev = device_info();
     if (!dev) return BOBA_ERR_CUDA;
     cudaStream_t stream = static_cast<cudaStream_t>(stream_);
-    const int mode = batch_mode();
     char *b = static_cast<char *>(ws);
     BatchArgs a;
     memset(&a, 0, sizeof(a));
@@ -821,6 +826,8 @@ extern "C" boba_status_t boba_reorder_batched(const int32_t *src, const int32_t 
     a.wmax = L.wmax;
     a.status = dev->status;
     a.large_threshold = kKcap;
+    a.small_max_m = mode == kBatchSplit ? kSmallMaxM : INT64_MAX;
+    a.n_limit = mode == kBatchSplit ? kMaxSize : (int64_t)kTeam * kKcap;
     if (mode == kBatchSplit) {
         uint32_t *tabs = reinterpret_cast<uint32_t *>(b + L.tabs);
         a.lg_pc = tabs;

@@ -136,8 +136,23 @@ def test_bad_offsets_are_skipped_and_reported(boba, mode):
 def test_size_limits(boba):
     z = torch.zeros(8, dtype=torch.int64, device="cuda")
     i = torch.zeros(8, dtype=torch.int32, device="cuda")
+    boba.boba_batched_set_mode(0)          # cluster mode: key array must fit a cluster
     assert boba.boba_reorder_batched(i, i, z, z, 1, 4, TEAM_MAX + 1, 4, 4, i, i, i, None, 0) == 3
+    boba.boba_batched_set_mode(-1)
     assert boba.boba_reorder_batched_workspace_bytes(4096, 1 << 23, TEAM_MAX, 1 << 31, 1 << 28) > 0
+
+
+def test_split_mode_takes_graphs_beyond_cluster_capacity(boba):
+    boba.boba_batched_set_mode(1)
+    graphs = []
+    for n, m, seed in ((TEAM_MAX + 5000, 900_000, 21), (3000, 40_000, 22), (1 << 20, 3_000_000, 23),
+                       (50_000, 2_500_000, 24)):                 # last: small n, many edges
+        scale = int(np.ceil(np.log2(n)))
+        I, J = synth.rmat(scale, m, seed=seed, n=n)
+        graphs.append((I, J, n))
+    src, dst, eo, vo = pack(graphs)
+    perm, so, do = run_batched(boba, src, dst, eo, vo)
+    check_against_oracle(graphs, perm, so, do, eo, vo)
 
 
 @pytest.mark.slow
