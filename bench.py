@@ -223,6 +223,16 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    tuning = None
+    if args.tune:
+        # autotune launch shapes on this workload (every variant checked bit-identical)
+        tuning = boba.tune_reorder(src, dst, n, reps=3)
+        if have_csr:
+            reorder()
+            csr()
+            tuning.update(boba.tune_spmv(row_ptr, col, val, x, reps=3))
+        boba.stream_status(stream)
+
     for _ in range(args.warmup):
         flush.zero_()
         step([torch.cuda.Event(enable_timing=True) for _ in range(4)])
@@ -294,6 +304,15 @@ def run_ours(args):
     e2e = None if args.no_e2e else run_e2e(args, boba, torch, dev, stream, src_h, dst_h, m, n,
                                            world)
 
+    serving = None
+    if args.serve and world == 1:
+        from paper_2306_10410_gb300 import serve as sv
+        serving = sv.serve_workload(n_requests=args.serve_requests, pool_size=args.serve_pool,
+                                    load=0.8, budget_bytes=120 << 30, spmv_iters=10)
+        serving = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in serving.items()}
+        serving["workload"] = ("Poisson stream of BOBA + CSR + 10x SpMV requests, R-MAT or grid, "
+                               "m log-uniform in [1e4, 1e8], offered load 0.8, HBM budget 120 GB")
+
     batched = None
     if args.batched and world == 1:
         del src_h, dst_h
@@ -312,6 +331,7 @@ def run_ours(args):
                       "csr": round(statistics.mean(t_csr), 4) if t_csr else None,
                       "spmv_total": round(statistics.mean(t_spmv), 4) if t_spmv else None},
         "reorder_roofline": reorder_roof,
+        "tuning": tuning,
         "orders": compare,
         "roofline": roof,
         "kernels": kern,
@@ -319,6 +339,7 @@ def run_ours(args):
         "clocks": clocks,
         "e2e": e2e,
         "batched": batched,
+        "serving": serving,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w, args)
@@ -415,6 +436,11 @@ def run_batched(args, boba, torch, dev, stream, flush, n_batch=4096, seed=None):
         return statistics.median(out)
 
     reps = max(3, min(args.steps, 5))
+    tuned = None
+    if args.tune:
+        tuned = boba.tune_batched(src, dst, eo_d, vo_d, max_m, max_n, reps=2)
+        ws = torch.empty(boba.boba_reorder_batched_workspace_bytes(n_batch, max_m, max_n, E, V),
+                         dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
         batched(stream)
     t_batched = timed(batched, reps)
@@ -448,6 +474,7 @@ def run_batched(args, boba, torch, dev, stream, flush, n_batch=4096, seed=None):
             "per_graph_gedges_s": round(E / (t_pergraph * 1e-3) / 1e9, 3),
             "speedup_batched_vs_per_graph": round(t_pergraph / t_batched, 3),
             "cuda_graph_ms": t_graph,
+            "schedule": {0: "split", 1: "cluster"}.get((tuned or {}).get("batched", 0)),
             "bit_identical": identical}
 
 
@@ -576,6 +603,12 @@ def main():
     ap.add_argument("--batched", type=int, default=1,
                     help="1: also time the batched workload (4096 graphs) vs per-graph launches")
     ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--tune", type=int, default=1,
+                    help="1: autotune launch variants on the workload before timing")
+    ap.add_argument("--serve", type=int, default=1,
+                    help="1: also run the serving workload (Poisson requests, HBM budget)")
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-pool", type=int, default=24)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)        # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -312,6 +312,59 @@ const char *boba_status_string(boba_status_t status);
 const char *boba_version(void);
 
 /* ------------------------------------------------------------------------
+ * Autotuning (launch shapes and schedules; results never change)
+ * ------------------------------------------------------------------------ */
+
+/* Kernel families with tuned variants (the `kernel` argument below). */
+enum { BOBA_TUNE_FIRST = 0, BOBA_TUNE_RELABEL = 1, BOBA_TUNE_BATCHED = 2, BOBA_TUNE_SPMV = 3 };
+
+/*
+ * boba_tune_reorder -- times every variant (block size x loads in flight) of
+ * the first-occurrence kernel, then of the relabel kernel, on this graph with
+ * boba_reorder_ex's arguments, discards any variant whose perm/src_out/dst_out
+ * differ from the default's in a single bit, and keeps the fastest for graphs
+ * in the same power-of-two size class of m on this device.  chosen (int[2],
+ * nullable) receives the picked variants.  Synchronous; allocates a reference
+ * copy of the outputs with cudaMalloc.  Not for use during stream capture.
+ */
+boba_status_t boba_tune_reorder(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                                int32_t *perm_out, int32_t *src_out, int32_t *dst_out,
+                                void *ws, size_t ws_bytes, int reps, int *chosen, void *stream);
+
+/*
+ * boba_tune_batched -- the same for the schedule of boba_reorder_batched
+ * (variant 0: split mode, 1: cluster mode), keyed by total_m.  A variant
+ * that needs more scratch than ws_bytes is skipped.  An explicit
+ * boba_batched_set_mode overrides the tuned choice.
+ */
+boba_status_t boba_tune_batched(const int32_t *src, const int32_t *dst, const int64_t *edge_off,
+                                const int64_t *vert_off, int64_t G, int64_t max_m, int64_t max_n,
+                                int64_t total_m, int64_t total_n, int32_t *perm_out,
+                                int32_t *src_out, int32_t *dst_out, void *ws, size_t ws_bytes,
+                                int reps, int *chosen, void *stream);
+
+/*
+ * boba_tune_spmv -- the same for the lanes per row of boba_spmv_csr
+ * (variant 0: chosen from nnz / n_rows; 1..4: 4, 8, 16, 32 lanes), keyed by
+ * nnz.  The variants sum in different orders, so their results may differ in
+ * the last bits; each is deterministic.
+ */
+boba_status_t boba_tune_spmv(const int64_t *row_ptr, const int32_t *col, const float *val,
+                             const float *x, float *y, int64_t n_rows, int64_t nnz, void *ws,
+                             size_t ws_bytes, int reps, int *chosen, void *stream);
+
+/* The tuned variant for a kernel family and size (0 = default), and setting it
+ * by hand (variant -1 clears it). */
+int boba_tune_get(int kernel, int64_t size);
+void boba_tune_set(int kernel, int64_t size, int variant);
+
+/* Persist / restore the choices of the current device (a text file, one line
+ * per choice, keyed by GPU name); reset clears every choice. */
+boba_status_t boba_tune_save(const char *path);
+boba_status_t boba_tune_load(const char *path);
+void boba_tune_reset(void);
+
+/* ------------------------------------------------------------------------
  * Kernel timing (a measurement aid for the evaluation of Sec. 5)
  * ------------------------------------------------------------------------ */
 

@@ -17,8 +17,11 @@ __all__ = [
     "boba_reorder", "boba_reorder_ex", "boba_reorder_workspace_bytes", "boba_reorder_static", "boba_reorder_batched",
     "boba_reorder_batched_workspace_bytes", "boba_batched_set_mode", "boba_coo_to_csr", "boba_coo_to_csr_workspace_bytes",
     "boba_spmv_csr", "boba_spmv_workspace_bytes", "boba_stream_status", "boba_status_string",
-    "Workspace", "kernel_timing",
+    "Workspace", "kernel_timing", "tune_reorder", "tune_batched", "tune_spmv", "tune_save",
+    "tune_load", "tune_reset", "TUNE_FIRST", "TUNE_RELABEL", "TUNE_BATCHED", "TUNE_SPMV",
 ]
+
+TUNE_FIRST, TUNE_RELABEL, TUNE_BATCHED, TUNE_SPMV = 0, 1, 2, 3
 
 
 def _p(t):
@@ -251,3 +254,66 @@ class kernel_timing:
                        for i in range(k)}
         lib.boba_timing_reset()
         return False
+
+
+# ---------------------------------------------------------------------------
+# autotuning
+# ---------------------------------------------------------------------------
+
+def _i2():
+    import ctypes
+    return (ctypes.c_int * 2)()
+
+
+def tune_reorder(src, dst, n, *, reps=3, ws=None, stream=None):
+    """Pick the fastest bit-identical first-occurrence / relabel variants for this size."""
+    m = src.numel()
+    perm = torch.empty(n, dtype=torch.int32, device=src.device)
+    so, do = torch.empty_like(src), torch.empty_like(dst)
+    buf = _ws(ws, boba_reorder_workspace_bytes(m, n), src.device)
+    ch = _i2()
+    check(load().boba_tune_reorder(_p(src), _p(dst), m, n, _p(perm), _p(so), _p(do), _p(buf),
+                                   buf.numel(), reps, ch, _s(stream)), "boba_tune_reorder")
+    return {"first": ch[0], "relabel": ch[1]}
+
+
+def tune_batched(src, dst, edge_off, vert_off, max_m, max_n, *, reps=3, stream=None):
+    G = edge_off.numel() - 1
+    total_m, total_n = src.numel(), int(vert_off[-1].item())
+    perm = torch.empty(total_n, dtype=torch.int32, device=src.device)
+    so, do = torch.empty_like(src), torch.empty_like(dst)
+    lib = load()
+    sizes = []
+    for mode in (0, 1):                       # scratch for whichever schedule is tried
+        lib.boba_batched_set_mode(mode)
+        sizes.append(lib.boba_reorder_batched_workspace_bytes(G, max_m, max_n, total_m, total_n))
+    lib.boba_batched_set_mode(-1)
+    nbytes = max(sizes)
+    buf = torch.empty(nbytes, dtype=torch.uint8, device=src.device)
+    ch = _i2()
+    check(load().boba_tune_batched(_p(src), _p(dst), _p(edge_off), _p(vert_off), G, max_m, max_n,
+                                   total_m, total_n, _p(perm), _p(so), _p(do), _p(buf), buf.numel(),
+                                   reps, ch, _s(stream)), "boba_tune_batched")
+    return {"batched": ch[0]}
+
+
+def tune_spmv(row_ptr, col, val, x, *, reps=3, stream=None):
+    n_rows, nnz = row_ptr.numel() - 1, col.numel()
+    y = torch.empty(n_rows, dtype=torch.float32, device=x.device)
+    buf = _ws(None, boba_spmv_workspace_bytes(n_rows, nnz), x.device)
+    ch = _i2()
+    check(load().boba_tune_spmv(_p(row_ptr), _p(col), _p(val), _p(x), _p(y), n_rows, nnz, _p(buf),
+                                buf.numel(), reps, ch, _s(stream)), "boba_tune_spmv")
+    return {"spmv": ch[0]}
+
+
+def tune_save(path):
+    check(load().boba_tune_save(str(path).encode()), "boba_tune_save")
+
+
+def tune_load(path):
+    check(load().boba_tune_load(str(path).encode()), "boba_tune_load")
+
+
+def tune_reset():
+    load().boba_tune_reset()

@@ -51,6 +51,15 @@ SIGNATURES = {
     "boba_server_drain": (_ST, [_P]),
     "boba_server_stats": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "boba_server_destroy": (None, [_P]),
+    "boba_tune_reorder": (_ST, [_P, _P, _I64, _I64, _P, _P, _P, _P, _SZ, ctypes.c_int, _P, _P]),
+    "boba_tune_batched": (_ST, [_P, _P, _P, _P, _I64, _I64, _I64, _I64, _I64, _P, _P, _P, _P,
+                                _SZ, ctypes.c_int, _P, _P]),
+    "boba_tune_spmv": (_ST, [_P, _P, _P, _P, _P, _I64, _I64, _P, _SZ, ctypes.c_int, _P, _P]),
+    "boba_tune_get": (ctypes.c_int, [ctypes.c_int, _I64]),
+    "boba_tune_set": (None, [ctypes.c_int, _I64, ctypes.c_int]),
+    "boba_tune_save": (_ST, [ctypes.c_char_p]),
+    "boba_tune_load": (_ST, [ctypes.c_char_p]),
+    "boba_tune_reset": (None, []),
     "boba_timing_enable": (None, [ctypes.c_int]),
     "boba_timing_collect": (ctypes.c_int, []),
     "boba_timing_name": (ctypes.c_char_p, [ctypes.c_int]),

@@ -726,11 +726,15 @@ const BatchDevice *batch_device()
     return &d;
 }
 
-int batch_mode()
+// Explicit setting, else the autotuned choice for this size, else the
+// environment, else split.
+int batch_mode(int64_t total_m)
 {
     if (g_mode_override >= 0) return g_mode_override;
+    const int v = tuned_variant(kTuneBatched, total_m);      // 0 split, 1 cluster
+    if (v == 1) return kBatchCluster;
     const char *e = getenv("BOBA_BATCH_MODE");
-    if (e && strcmp(e, "cluster") == 0) return kBatchCluster;
+    if (v == 0 && e && strcmp(e, "cluster") == 0) return kBatchCluster;
     return kBatchSplit;
 }
 
@@ -776,7 +780,8 @@ extern "C" size_t boba_reorder_batched_workspace_bytes(int64_t G, int64_t max_m,
                                                        int64_t total_m, int64_t total_n)
 {
     BatchLayout L;
-    if (!batch_layout(G, max_m, max_n, total_m, total_n, batch_device(), batch_mode(), L)) return 0;
+    if (!batch_layout(G, max_m, max_n, total_m, total_n, batch_device(), batch_mode(total_m), L))
+        return 0;
     return L.total;
 }
 
@@ -789,7 +794,7 @@ extern "C" boba_status_t boba_reorder_batched(const int32_t *src, const int32_t 
 {
     if (G < 0 || max_m < 0 || max_n < 0 || total_m < 0 || total_n < 0) return BOBA_ERR_INVALID_ARG;
     if (max_m > kMaxSize || max_n > kMaxSize) return BOBA_ERR_TOO_LARGE;
-    const int mode = batch_mode();
+    const int mode = batch_mode(total_m);
     if (mode == kBatchCluster && max_n > (int64_t)kTeam * kKcap) return BOBA_ERR_TOO_LARGE;
     if (G == 0) return BOBA_OK;
     if (edge_off == nullptr || vert_off == nullptr) return BOBA_ERR_INVALID_ARG;

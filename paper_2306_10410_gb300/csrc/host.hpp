@@ -46,6 +46,13 @@ bool timing_on();
 void timing_begin(const char *name, cudaStream_t s, int *slot);
 void timing_end(int slot, cudaStream_t s);
 
+// Autotuned choices: the variant index picked for a kernel family and a size
+// (bucketed by log2 of the size), or 0 (the default variant) if none.
+enum TuneKernel { kTuneFirst = 0, kTuneRelabel = 1, kTuneBatched = 2, kTuneSpmv = 3,
+                  kTuneKernels = 4 };
+int tuned_variant(int kernel, int64_t size);
+int size_class(int64_t size);
+
 }  // namespace boba
 
 // BOBA_TIMED("name", stream, kernel<<<g, b, smem, stream>>>(args));

@@ -49,16 +49,15 @@ __global__ void __launch_bounds__(256) k_init(uint32_t *__restrict__ key, int64_
 // read most earlier positions are already recorded and the filtering read
 // (key[v] <= i) skips the atomic.
 // ---------------------------------------------------------------------------
-template <bool VEC>
-__global__ void __launch_bounds__(kFirstBlock) k_first(const int32_t *__restrict__ src,
+template <bool VEC, int BLOCK, int U>
+__device__ __forceinline__ void first_body(const int32_t *__restrict__ src,
                                                        const int32_t *__restrict__ dst, int64_t m,
                                                        uint32_t n, uint32_t *key, uint32_t *status)
 {
-    constexpr int U = kFirstUnroll;
     const int64_t Q = VEC ? (m >> 2) : 0;   // full int4 quads per half
     if (VEC) {
         const int64_t total = 2 * Q;
-        const int64_t chunk = (int64_t)kFirstBlock * U;
+        const int64_t chunk = (int64_t)BLOCK * U;
         const int64_t step = (int64_t)gridDim.x * chunk;
         for (int64_t base = (int64_t)blockIdx.x * chunk; base < total; base += step) {
             int4 q[U];
@@ -66,7 +65,7 @@ __global__ void __launch_bounds__(kFirstBlock) k_first(const int32_t *__restrict
             bool ok[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int64_t g = base + u * kFirstBlock + threadIdx.x;
+                const int64_t g = base + u * BLOCK + threadIdx.x;
                 ok[u] = g < total;
                 if (ok[u]) {
                     const bool hi = g >= Q;
@@ -109,6 +108,23 @@ __global__ void __launch_bounds__(kFirstBlock) k_first(const int32_t *__restrict
         if ((uint32_t)v >= n) raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE);
         else first_update(v, pos, key[v], key);
     }
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(kFirstBlock) k_first(const int32_t *__restrict__ src,
+                                                       const int32_t *__restrict__ dst, int64_t m,
+                                                       uint32_t n, uint32_t *key, uint32_t *status)
+{
+    first_body<VEC, kFirstBlock, kFirstUnroll>(src, dst, m, n, key, status);
+}
+
+// Variants for the autotuner (vector path): BLOCK threads, U int4 loads in flight.
+template <int BLOCK, int U>
+__global__ void __launch_bounds__(BLOCK) k_first_v(const int32_t *__restrict__ src,
+                                                   const int32_t *__restrict__ dst, int64_t m,
+                                                   uint32_t n, uint32_t *key, uint32_t *status)
+{
+    first_body<true, BLOCK, U>(src, dst, m, n, key, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -223,24 +239,23 @@ __global__ void __launch_bounds__(kEmitBlock) k_emit(const uint32_t *__restrict_
 // kept.  src_out/dst_out may alias src/dst: each element is read before the
 // same thread writes it.
 // ---------------------------------------------------------------------------
-template <bool VEC>
-__global__ void __launch_bounds__(kRelabelBlock) k_relabel(const int32_t *src, const int32_t *dst,
+template <bool VEC, int BLOCK, int U>
+__device__ __forceinline__ void relabel_body(const int32_t *src, const int32_t *dst,
                                                            int64_t m, uint32_t n,
                                                            const int32_t *__restrict__ label,
                                                            int32_t *src_out, int32_t *dst_out,
                                                            uint32_t *status)
 {
-    constexpr int U = kRelabelUnroll;
     const int64_t Q = VEC ? (m >> 2) : 0;
     if (VEC) {
         const int64_t total = 2 * Q;
-        const int64_t chunk = (int64_t)kRelabelBlock * U;
+        const int64_t chunk = (int64_t)BLOCK * U;
         const int64_t step = (int64_t)gridDim.x * chunk;
         for (int64_t base = (int64_t)blockIdx.x * chunk; base < total; base += step) {
             int4 q[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int64_t g = base + u * kRelabelBlock + threadIdx.x;
+                const int64_t g = base + u * BLOCK + threadIdx.x;
                 if (g < total) {
                     const bool hi = g >= Q;
                     q[u] = ld_stream(reinterpret_cast<const int4 *>(hi ? dst : src) + (hi ? g - Q : g));
@@ -248,7 +263,7 @@ __global__ void __launch_bounds__(kRelabelBlock) k_relabel(const int32_t *src, c
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int64_t g = base + u * kRelabelBlock + threadIdx.x;
+                const int64_t g = base + u * BLOCK + threadIdx.x;
                 if (g < total) {
                     int4 r;
                     int32_t *rr = &r.x;
@@ -263,7 +278,7 @@ __global__ void __launch_bounds__(kRelabelBlock) k_relabel(const int32_t *src, c
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int64_t g = base + u * kRelabelBlock + threadIdx.x;
+                const int64_t g = base + u * BLOCK + threadIdx.x;
                 if (g < total) {
                     const bool hi = g >= Q;
                     st_stream(reinterpret_cast<int4 *>(hi ? dst_out : src_out) + (hi ? g - Q : g), q[u]);
@@ -281,6 +296,71 @@ __global__ void __launch_bounds__(kRelabelBlock) k_relabel(const int32_t *src, c
         if ((uint32_t)v < n) r = __ldg(label + v);
         else { r = -1; raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE); }
         (hi ? dst_out : src_out)[e] = r;
+    }
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(kRelabelBlock) k_relabel(const int32_t *src, const int32_t *dst,
+                                                           int64_t m, uint32_t n,
+                                                           const int32_t *__restrict__ label,
+                                                           int32_t *src_out, int32_t *dst_out,
+                                                           uint32_t *status)
+{
+    relabel_body<VEC, kRelabelBlock, kRelabelUnroll>(src, dst, m, n, label, src_out, dst_out, status);
+}
+
+template <int BLOCK, int U>
+__global__ void __launch_bounds__(BLOCK) k_relabel_v(const int32_t *src, const int32_t *dst,
+                                                     int64_t m, uint32_t n,
+                                                     const int32_t *__restrict__ label,
+                                                     int32_t *src_out, int32_t *dst_out,
+                                                     uint32_t *status)
+{
+    relabel_body<true, BLOCK, U>(src, dst, m, n, label, src_out, dst_out, status);
+}
+
+// Launch one tuned variant of the vector-path first-occurrence / relabel kernel.
+template <int BLOCK, int U>
+void launch_first_v(const ReorderArgs &a, cudaStream_t stream)
+{
+    const int64_t work = cdiv(2 * a.m, 4LL * BLOCK * U);
+    const int g = persistent_grid((const void *)k_first_v<BLOCK, U>, BLOCK, work);
+    BOBA_TIMED("reorder.first", stream,
+               k_first_v<BLOCK, U><<<g, BLOCK, 0, stream>>>(a.src, a.dst, a.m, a.n, a.key, a.status));
+}
+
+template <int BLOCK, int U>
+void launch_relabel_v(const ReorderArgs &a, cudaStream_t stream)
+{
+    const int64_t work = cdiv(2 * a.m, 4LL * BLOCK * U);
+    const int g = persistent_grid((const void *)k_relabel_v<BLOCK, U>, BLOCK, work);
+    BOBA_TIMED("reorder.relabel", stream,
+               k_relabel_v<BLOCK, U><<<g, BLOCK, 0, stream>>>(a.src, a.dst, a.m, a.n, a.label,
+                                                              a.src_out, a.dst_out, a.status));
+}
+
+// Variant table: index -> (block, loads in flight).  Index 0 is the default.
+bool launch_first_variant(int v, const ReorderArgs &a, cudaStream_t s)
+{
+    switch (v) {
+    case 1: launch_first_v<256, 2>(a, s); return true;
+    case 2: launch_first_v<256, 8>(a, s); return true;
+    case 3: launch_first_v<512, 4>(a, s); return true;
+    case 4: launch_first_v<128, 8>(a, s); return true;
+    case 5: launch_first_v<512, 2>(a, s); return true;
+    default: return false;
+    }
+}
+
+bool launch_relabel_variant(int v, const ReorderArgs &a, cudaStream_t s)
+{
+    switch (v) {
+    case 1: launch_relabel_v<256, 2>(a, s); return true;
+    case 2: launch_relabel_v<256, 8>(a, s); return true;
+    case 3: launch_relabel_v<512, 4>(a, s); return true;
+    case 4: launch_relabel_v<128, 8>(a, s); return true;
+    case 5: launch_relabel_v<512, 2>(a, s); return true;
+    default: return false;
     }
 }
 
@@ -307,7 +387,9 @@ boba_status_t launch_reorder(const ReorderArgs &a, int64_t n4, size_t nzero_u32,
     if (a.m > 0) {
         const bool vec = aligned16(a.src) && aligned16(a.dst);
         const int64_t work = cdiv(2 * a.m, 4 * kFirstBlock * kFirstUnroll);
-        if (vec) {
+        if (vec && launch_first_variant(tuned_variant(kTuneFirst, a.m), a, stream)) {
+            // tuned variant launched
+        } else if (vec) {
             const int g = persistent_grid((const void *)k_first<true>, kFirstBlock, work);
             BOBA_TIMED("reorder.first", stream,
                        k_first<true><<<g, kFirstBlock, 0, stream>>>(a.src, a.dst, a.m, a.n, a.key,
@@ -332,7 +414,9 @@ boba_status_t launch_reorder(const ReorderArgs &a, int64_t n4, size_t nzero_u32,
         const bool vec = aligned16(a.src) && aligned16(a.dst) && aligned16(a.src_out) &&
                          aligned16(a.dst_out);
         const int64_t work = cdiv(2 * a.m, 4 * kRelabelBlock * kRelabelUnroll);
-        if (vec) {
+        if (vec && launch_relabel_variant(tuned_variant(kTuneRelabel, a.m), a, stream)) {
+            // tuned variant launched
+        } else if (vec) {
             const int g = persistent_grid((const void *)k_relabel<true>, kRelabelBlock, work);
             BOBA_TIMED("reorder.relabel", stream,
                        k_relabel<true><<<g, kRelabelBlock, 0, stream>>>(

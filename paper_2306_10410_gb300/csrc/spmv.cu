@@ -209,7 +209,12 @@ extern "C" boba_status_t boba_spmv_csr(const int64_t *row_ptr, const int32_t *co
 
     BOBA_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t), stream));
     const double avg = (double)nnz / (double)n_rows;
-    if (avg <= 6.0) launch_rows<4>(row_ptr, col, val, x, y, n_rows, cnt, list, cap, dev->status, stream);
+    const int tv = tuned_variant(kTuneSpmv, nnz);           // 0 auto, 1..4: LPR 4, 8, 16, 32
+    if (tv == 1) launch_rows<4>(row_ptr, col, val, x, y, n_rows, cnt, list, cap, dev->status, stream);
+    else if (tv == 2) launch_rows<8>(row_ptr, col, val, x, y, n_rows, cnt, list, cap, dev->status, stream);
+    else if (tv == 3) launch_rows<16>(row_ptr, col, val, x, y, n_rows, cnt, list, cap, dev->status, stream);
+    else if (tv == 4) launch_rows<32>(row_ptr, col, val, x, y, n_rows, cnt, list, cap, dev->status, stream);
+    else if (avg <= 6.0) launch_rows<4>(row_ptr, col, val, x, y, n_rows, cnt, list, cap, dev->status, stream);
     else if (avg <= 12.0) launch_rows<8>(row_ptr, col, val, x, y, n_rows, cnt, list, cap, dev->status, stream);
     else if (avg <= 24.0) launch_rows<16>(row_ptr, col, val, x, y, n_rows, cnt, list, cap, dev->status, stream);
     else launch_rows<32>(row_ptr, col, val, x, y, n_rows, cnt, list, cap, dev->status, stream);
