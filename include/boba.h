@@ -139,6 +139,44 @@ boba_status_t boba_reorder_static(const int32_t *src, const int32_t *dst, int64_
                                   uint32_t *error_bits, void *stream);
 
 /* ------------------------------------------------------------------------
+ * The reorder's phases as separate calls (sharding one graph over devices)
+ * ------------------------------------------------------------------------ */
+
+/*
+ * boba_first_keys -- lowers key[v] to the lowest position of v among the
+ * given edges (Alg. 2 with AtomicMin, Sec. 4.5), where local edge e holds
+ * positions pos_src + e (its source) and pos_dst + e (its destination) of the
+ * global stream I ++ J.  For a shard [e0, e1) of a graph with m edges, pass
+ * the shard's arrays with pos_src = e0, pos_dst = m + e0.
+ *   key   uint32[n] (device); init != 0 first sets every key to 0xFFFFFFFF
+ * Keys of different shards combine by an elementwise MIN (all-reduce); the
+ * result equals the keys of the whole graph.  Positions must stay < 2^32 - 1.
+ */
+boba_status_t boba_first_keys(const int32_t *src, const int32_t *dst, int64_t m_local,
+                              int64_t pos_src, int64_t pos_dst, int64_t n, uint32_t *key,
+                              int init, void *stream);
+
+/* Scratch bytes for boba_labels_from_keys. */
+size_t boba_labels_workspace_bytes(int64_t m_total, int64_t n);
+
+/*
+ * boba_labels_from_keys -- ParMapKeys (Alg. 2): from complete keys of a graph
+ * with m_total edges, perm_out[k] = v and label_out[v] = k (label_out may be
+ * NULL), vertices on no edge last in ascending ID.  key is not modified.
+ */
+boba_status_t boba_labels_from_keys(const uint32_t *key, int64_t m_total, int64_t n,
+                                    int32_t *perm_out, int32_t *label_out, void *ws,
+                                    size_t ws_bytes, void *stream);
+
+/*
+ * boba_relabel -- src_out[e] = label[src[e]], dst_out[e] = label[dst[e]]
+ * (Sec. 5.3); outputs may alias inputs.  Out-of-range IDs give -1.
+ */
+boba_status_t boba_relabel(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                           const int32_t *label, int32_t *src_out, int32_t *dst_out,
+                           void *stream);
+
+/* ------------------------------------------------------------------------
  * Batched reordering: G independent graphs in one persistent launch
  * ------------------------------------------------------------------------ */
 

@@ -52,7 +52,8 @@ __global__ void __launch_bounds__(256) k_init(uint32_t *__restrict__ key, int64_
 template <bool VEC, int BLOCK, int U>
 __device__ __forceinline__ void first_body(const int32_t *__restrict__ src,
                                                        const int32_t *__restrict__ dst, int64_t m,
-                                                       uint32_t n, uint32_t *key, uint32_t *status)
+                                                       uint32_t n, uint32_t *key, uint32_t *status,
+                                                       int64_t pos_src, int64_t pos_dst)
 {
     const int64_t Q = VEC ? (m >> 2) : 0;   // full int4 quads per half
     if (VEC) {
@@ -71,7 +72,7 @@ __device__ __forceinline__ void first_body(const int32_t *__restrict__ src,
                     const bool hi = g >= Q;
                     const int64_t qi = hi ? g - Q : g;
                     q[u] = ld_stream(reinterpret_cast<const int4 *>(hi ? dst : src) + qi);
-                    p0[u] = (uint32_t)((hi ? m : 0) + 4 * qi);
+                    p0[u] = (uint32_t)((hi ? pos_dst : pos_src) + 4 * qi);
                 } else {
                     q[u] = make_int4(0, 0, 0, 0);
                     p0[u] = 0;
@@ -104,7 +105,7 @@ __device__ __forceinline__ void first_body(const int32_t *__restrict__ src,
         const bool hi = t >= rem;
         const int64_t e = 4 * Q + (hi ? t - rem : t);
         const int32_t v = ld_stream((hi ? dst : src) + e);
-        const uint32_t pos = (uint32_t)((hi ? m : 0) + e);
+        const uint32_t pos = (uint32_t)((hi ? pos_dst : pos_src) + e);
         if ((uint32_t)v >= n) raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE);
         else first_update(v, pos, key[v], key);
     }
@@ -115,7 +116,18 @@ __global__ void __launch_bounds__(kFirstBlock) k_first(const int32_t *__restrict
                                                        const int32_t *__restrict__ dst, int64_t m,
                                                        uint32_t n, uint32_t *key, uint32_t *status)
 {
-    first_body<VEC, kFirstBlock, kFirstUnroll>(src, dst, m, n, key, status);
+    first_body<VEC, kFirstBlock, kFirstUnroll>(src, dst, m, n, key, status, 0, m);
+}
+
+// Positions from explicit bases: local edge e holds positions pos_src + e and
+// pos_dst + e of the global I ++ J (a shard of a larger graph).
+template <bool VEC>
+__global__ void __launch_bounds__(kFirstBlock) k_first_at(const int32_t *__restrict__ src,
+                                                          const int32_t *__restrict__ dst, int64_t m,
+                                                          uint32_t n, uint32_t *key, uint32_t *status,
+                                                          int64_t pos_src, int64_t pos_dst)
+{
+    first_body<VEC, kFirstBlock, kFirstUnroll>(src, dst, m, n, key, status, pos_src, pos_dst);
 }
 
 // Variants for the autotuner (vector path): BLOCK threads, U int4 loads in flight.
@@ -124,7 +136,7 @@ __global__ void __launch_bounds__(BLOCK) k_first_v(const int32_t *__restrict__ s
                                                    const int32_t *__restrict__ dst, int64_t m,
                                                    uint32_t n, uint32_t *key, uint32_t *status)
 {
-    first_body<true, BLOCK, U>(src, dst, m, n, key, status);
+    first_body<true, BLOCK, U>(src, dst, m, n, key, status, 0, m);
 }
 
 // ---------------------------------------------------------------------------
@@ -484,4 +496,139 @@ extern "C" boba_status_t boba_reorder_ex(const int32_t *src, const int32_t *dst,
     a.dst_out = dst_out;
     a.label_vec = aligned16(a.label);
     return launch_reorder(a, L.n4, (L.zero_end - L.zero_begin) / 4, stream);
+}
+
+// ---------------------------------------------------------------------------
+// The three phases as separate entry points (for sharding a graph over
+// several devices: local keys, a MIN merge of the key arrays, then labels and
+// relabel on every device).
+// ---------------------------------------------------------------------------
+
+extern "C" boba_status_t boba_first_keys(const int32_t *src, const int32_t *dst, int64_t m_local,
+                                         int64_t pos_src, int64_t pos_dst, int64_t n,
+                                         uint32_t *key, int init, void *stream_)
+{
+    if (m_local < 0 || n < 0 || pos_src < 0 || pos_dst < 0) return BOBA_ERR_INVALID_ARG;
+    if (m_local > kMaxSize || n > kMaxSize) return BOBA_ERR_TOO_LARGE;
+    if (pos_src + m_local > 2 * kMaxSize || pos_dst + m_local > 2 * kMaxSize) return BOBA_ERR_TOO_LARGE;
+    if (n == 0) return m_local == 0 ? BOBA_OK : BOBA_ERR_INVALID_ARG;
+    if (key == nullptr || (m_local > 0 && (src == nullptr || dst == nullptr))) return BOBA_ERR_INVALID_ARG;
+    const DeviceInfo *dev = device_info();
+    if (!dev) return BOBA_ERR_CUDA;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    if (init) BOBA_CUDA_TRY(cudaMemsetAsync(key, 0xFF, (size_t)n * 4, stream));
+    if (m_local > 0) {
+        const bool vec = aligned16(src) && aligned16(dst);
+        const int64_t work = cdiv(2 * m_local, 4 * kFirstBlock * kFirstUnroll);
+        if (vec) {
+            const int g = persistent_grid((const void *)k_first_at<true>, kFirstBlock, work);
+            BOBA_TIMED("reorder.first", stream,
+                       k_first_at<true><<<g, kFirstBlock, 0, stream>>>(src, dst, m_local, (uint32_t)n,
+                                                                      key, dev->status, pos_src,
+                                                                      pos_dst));
+        } else {
+            const int g = persistent_grid((const void *)k_first_at<false>, kFirstBlock, work * 4);
+            BOBA_TIMED("reorder.first", stream,
+                       k_first_at<false><<<g, kFirstBlock, 0, stream>>>(src, dst, m_local,
+                                                                       (uint32_t)n, key,
+                                                                       dev->status, pos_src,
+                                                                       pos_dst));
+        }
+    }
+    BOBA_LAUNCH_CHECK();
+    return BOBA_OK;
+}
+
+extern "C" size_t boba_labels_workspace_bytes(int64_t m_total, int64_t n)
+{
+    return boba_reorder_workspace_bytes(m_total, n);
+}
+
+extern "C" boba_status_t boba_labels_from_keys(const uint32_t *key, int64_t m_total, int64_t n,
+                                               int32_t *perm_out, int32_t *label_out, void *ws,
+                                               size_t ws_bytes, void *stream_)
+{
+    if (m_total < 0 || n < 0) return BOBA_ERR_INVALID_ARG;
+    if (m_total > kMaxSize || n > kMaxSize) return BOBA_ERR_TOO_LARGE;
+    if (n == 0) return BOBA_OK;
+    if (key == nullptr || perm_out == nullptr || ws == nullptr) return BOBA_ERR_INVALID_ARG;
+    ReorderLayout L;
+    reorder_layout(m_total, n, L);
+    if (ws_bytes < L.total || !aligned256(ws)) return BOBA_ERR_WORKSPACE;
+    const DeviceInfo *dev = device_info();
+    if (!dev) return BOBA_ERR_CUDA;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    char *base = static_cast<char *>(ws);
+    uint32_t *kcopy = reinterpret_cast<uint32_t *>(base + L.key);
+    // the kernels read keys padded to a multiple of 4 with SENT
+    const int64_t nzero = (int64_t)((L.zero_end - L.zero_begin) / 4);
+    {
+        const int64_t work = cdiv((L.n4 > nzero ? L.n4 : nzero) / 4, 256);
+        const int g = persistent_grid((const void *)k_init, 256, work);
+        BOBA_TIMED("reorder.init", stream,
+                   k_init<<<g, 256, 0, stream>>>(kcopy, L.n4,
+                                                 reinterpret_cast<uint32_t *>(base + L.bitmap), nzero));
+    }
+    BOBA_CUDA_TRY(cudaMemcpyAsync(kcopy, key, (size_t)n * 4, cudaMemcpyDeviceToDevice, stream));
+    ReorderArgs a;
+    a.src = nullptr;
+    a.dst = nullptr;
+    a.m = m_total;
+    a.n = (uint32_t)n;
+    a.key = kcopy;
+    a.label = label_out ? label_out : reinterpret_cast<int32_t *>(base + L.label);
+    a.perm = perm_out;
+    a.bitmap = reinterpret_cast<uint32_t *>(base + L.bitmap);
+    a.grp = reinterpret_cast<uint32_t *>(base + L.grp);
+    a.tstat_scan = reinterpret_cast<uint64_t *>(base + L.tstat_scan);
+    a.tstat_emit = reinterpret_cast<uint64_t *>(base + L.tstat_emit);
+    a.counters = reinterpret_cast<uint32_t *>(base + L.counters);
+    a.nwords = L.nwords;
+    a.scan_tiles = L.scan_tiles;
+    a.emit_tiles = L.emit_tiles;
+    a.status = dev->status;
+    a.src_out = nullptr;
+    a.dst_out = nullptr;
+    a.label_vec = aligned16(a.label);
+    if (m_total > 0) {
+        const int gm = persistent_grid((const void *)k_mark, 256, cdiv(L.n4 / 4, 256));
+        BOBA_TIMED("reorder.mark", stream, k_mark<<<gm, 256, 0, stream>>>(a.key, L.n4, a.bitmap));
+        BOBA_TIMED("reorder.scan", stream,
+                   k_scan<<<(unsigned)a.scan_tiles, kScanBlock, 0, stream>>>(
+                       a.bitmap, a.grp, a.tstat_scan, a.counters, a.scan_tiles, a.status));
+    }
+    BOBA_TIMED("reorder.emit", stream,
+               k_emit<<<(unsigned)a.emit_tiles, kEmitBlock, 0, stream>>>(
+                   a.key, a.n, a.bitmap, a.grp, a.label, a.perm, a.tstat_emit, a.counters,
+                   a.label_vec, a.status));
+    BOBA_LAUNCH_CHECK();
+    return BOBA_OK;
+}
+
+extern "C" boba_status_t boba_relabel(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                                      const int32_t *label, int32_t *src_out, int32_t *dst_out,
+                                      void *stream_)
+{
+    if (m < 0 || n < 0) return BOBA_ERR_INVALID_ARG;
+    if (m > kMaxSize || n > kMaxSize) return BOBA_ERR_TOO_LARGE;
+    if (m == 0) return BOBA_OK;
+    if (!src || !dst || !label || !src_out || !dst_out) return BOBA_ERR_INVALID_ARG;
+    const DeviceInfo *dev = device_info();
+    if (!dev) return BOBA_ERR_CUDA;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    const bool vec = aligned16(src) && aligned16(dst) && aligned16(src_out) && aligned16(dst_out);
+    const int64_t work = cdiv(2 * m, 4 * kRelabelBlock * kRelabelUnroll);
+    if (vec) {
+        const int g = persistent_grid((const void *)k_relabel<true>, kRelabelBlock, work);
+        BOBA_TIMED("reorder.relabel", stream,
+                   k_relabel<true><<<g, kRelabelBlock, 0, stream>>>(src, dst, m, (uint32_t)n, label,
+                                                                   src_out, dst_out, dev->status));
+    } else {
+        const int g = persistent_grid((const void *)k_relabel<false>, kRelabelBlock, work * 4);
+        BOBA_TIMED("reorder.relabel", stream,
+                   k_relabel<false><<<g, kRelabelBlock, 0, stream>>>(src, dst, m, (uint32_t)n, label,
+                                                                    src_out, dst_out, dev->status));
+    }
+    BOBA_LAUNCH_CHECK();
+    return BOBA_OK;
 }

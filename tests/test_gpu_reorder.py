@@ -183,3 +183,49 @@ def test_full_size_bit_exact(boba, wname):
     w = synth.WORKLOADS[wname]
     I, J = w.generate()
     assert_parity(boba, I, J, w.n)
+
+
+@pytest.mark.parametrize("shards", [1, 2, 3, 5])
+def test_sharded_phases_equal_whole_graph(boba, shards):
+    """Keys of edge shards (global positions), merged by MIN, then labels and a
+    per-shard relabel: the same perm and edges as the one-call reorder."""
+    from paper_2306_10410_gb300 import dist as bd
+    lib = boba.load()
+    I, J = synth.rmat(16, 700_001, seed=44)
+    n, m = 1 << 16, len(I)
+    src, dst = torch.from_numpy(I).cuda(), torch.from_numpy(J).cuda()
+    merged = None
+    for r in range(shards):
+        e0, e1 = bd.shard_bounds(m, r, shards)
+        key = torch.empty(n, dtype=torch.int32, device="cuda")
+        s_, d_ = src[e0:e1].clone(), dst[e0:e1].clone()
+        assert lib.boba_first_keys(s_.data_ptr(), d_.data_ptr(), e1 - e0, e0, m + e0, n,
+                                   key.data_ptr(), 1, torch.cuda.current_stream().cuda_stream) == 0
+        w = bd.keys_to_wire(key)
+        merged = w if merged is None else torch.minimum(merged, w)
+    key = bd.wire_to_keys(merged)
+    okey = oracle.first_keys(I, J, n)
+    np.testing.assert_array_equal(key.cpu().numpy().view(np.uint32), okey)
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    label = torch.empty(n, dtype=torch.int32, device="cuda")
+    ws = torch.empty(lib.boba_labels_workspace_bytes(m, n), dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    assert lib.boba_labels_from_keys(key.data_ptr(), m, n, perm.data_ptr(), label.data_ptr(),
+                                     ws.data_ptr(), ws.numel(), st) == 0
+    operm, oso, odo = oracle.reorder(I, J, n)
+    np.testing.assert_array_equal(perm.cpu().numpy(), operm)
+    for r in range(shards):
+        e0, e1 = bd.shard_bounds(m, r, shards)
+        so = torch.empty(e1 - e0, dtype=torch.int32, device="cuda")
+        do = torch.empty_like(so)
+        s_, d_ = src[e0:e1].clone(), dst[e0:e1].clone()
+        assert lib.boba_relabel(s_.data_ptr(), d_.data_ptr(), e1 - e0, n, label.data_ptr(),
+                                so.data_ptr(), do.data_ptr(), st) == 0
+        np.testing.assert_array_equal(so.cpu().numpy(), oso[e0:e1])
+        np.testing.assert_array_equal(do.cpu().numpy(), odo[e0:e1])
+    boba.stream_status()
+    # the helper, on one rank, is the plain reorder
+    p2, s2, d2 = bd.sharded_reorder(src, dst, m, n, 0)
+    boba.stream_status()
+    np.testing.assert_array_equal(p2.cpu().numpy(), operm)
+    np.testing.assert_array_equal(s2.cpu().numpy(), oso)
