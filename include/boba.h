@@ -313,10 +313,12 @@ size_t boba_coo_to_csr_workspace_bytes(int64_t m, int64_t n);
 
 /*
  * boba_spmv_csr -- y = A x for the CSR (row_ptr, col, val), Alg. 3 (pull),
- * fp32 products and fp32 accumulation.  Rows are processed warp-per-row, or
- * several short rows per warp, in a fixed order, so the result is the same
- * run to run.  Rows longer than a threshold are split across warps whose
- * partial sums are combined in a fixed order through the workspace.
+ * fp32 products and fp32 accumulation.  By default rows are processed
+ * warp-per-row, or several short rows per warp, in a fixed order, so the
+ * result is the same run to run; rows longer than a threshold are split
+ * across warps whose partial sums are combined in a fixed order through the
+ * workspace.  The merge-path variant (see boba_tune_spmv) splits the work
+ * evenly over row ends and nonzeros instead.
  *
  *   row_ptr int64[n_rows+1], col int32[nnz], val float[nnz] (device);
  *   x float[n_cols], y float[n_rows] (device; y must not alias x)
@@ -382,10 +384,11 @@ boba_status_t boba_tune_batched(const int32_t *src, const int32_t *dst, const in
                                 int reps, int *chosen, void *stream);
 
 /*
- * boba_tune_spmv -- the same for the lanes per row of boba_spmv_csr
- * (variant 0: chosen from nnz / n_rows; 1..4: 4, 8, 16, 32 lanes), keyed by
- * nnz.  The variants sum in different orders, so their results may differ in
- * the last bits; each is deterministic.
+ * boba_tune_spmv -- the same for boba_spmv_csr (variant 0: lanes per row
+ * chosen from nnz / n_rows; 1..4: 4, 8, 16, 32 lanes per row; 5: merge-path
+ * decomposition over row ends and nonzeros), keyed by nnz.  The variants sum
+ * in different orders, so their results may differ in the last bits; each is
+ * deterministic.
  */
 boba_status_t boba_tune_spmv(const int64_t *row_ptr, const int32_t *col, const float *val,
                              const float *x, float *y, int64_t n_rows, int64_t nnz, void *ws,

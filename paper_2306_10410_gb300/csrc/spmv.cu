@@ -24,9 +24,13 @@ constexpr int64_t kChunk = 16384;      // entries per chunk of a long row
 constexpr int kChunkBlock = 1024;
 constexpr int kRowsBlock = 256;
 
+constexpr int kMpBlock = 256;
+constexpr int kMpItems = 8;
+constexpr int kMpTile = kMpBlock * kMpItems;       // path items (row ends + nonzeros) per tile
+
 struct SpmvLayout {
-    int64_t cap, max_chunks;
-    size_t count, list, cstart, partial, total;
+    int64_t cap, max_chunks, mp_tiles;
+    size_t count, list, cstart, partial, mp_part, mp_crow, mp_cval, total;
 };
 
 bool spmv_layout(int64_t n_rows, int64_t nnz, SpmvLayout &L)
@@ -39,6 +43,10 @@ bool spmv_layout(int64_t n_rows, int64_t nnz, SpmvLayout &L)
     L.list = c.take((size_t)L.cap * 4);
     L.cstart = c.take((size_t)(L.cap + 1) * 4);
     L.partial = c.take((size_t)L.max_chunks * 4);
+    L.mp_tiles = cdiv(n_rows + nnz, kMpTile);
+    L.mp_part = c.take((size_t)(L.mp_tiles + 1) * 8);
+    L.mp_crow = c.take((size_t)(L.mp_tiles + 1) * 4);
+    L.mp_cval = c.take((size_t)(L.mp_tiles + 1) * 4);
     L.total = c.off;
     return true;
 }
@@ -158,6 +166,154 @@ __global__ void __launch_bounds__(256) k_spmv_gather(const uint32_t *long_count,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Merge-path SpMV (Merrill and Garland, "Merge-based parallel sparse matrix-
+// vector multiplication", SC 2016), the load balancing of the paper's
+// evaluation (Sec. 3.4): the path of n_rows row ends and nnz nonzeros is cut
+// into tiles of kMpTile items, so every block gets the same work whatever the
+// row lengths.  Sums run in path order within a thread, then a segmented scan
+// over the threads of a tile, then (for rows crossing tiles) the tiles'
+// carries in tile order: deterministic, but the rounding depends on where a
+// row falls relative to the tiles.
+// ---------------------------------------------------------------------------
+
+// Split of diagonal d of the merge of row_ptr[1..n] with 0..nnz-1: x row ends
+// and y nonzeros lie before it (x + y = d).
+__device__ __forceinline__ void mp_search(const int64_t *__restrict__ row_ptr, int64_t n,
+                                          int64_t nnz, int64_t d, int64_t &x, int64_t &y)
+{
+    int64_t lo = d - nnz > 0 ? d - nnz : 0, hi = d < n ? d : n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (__ldg(row_ptr + mid + 1) <= d - mid - 1) lo = mid + 1;
+        else hi = mid;
+    }
+    x = lo;
+    y = d - lo;
+}
+
+__global__ void __launch_bounds__(256) k_mp_partition(const int64_t *__restrict__ row_ptr, int64_t n,
+                                                      int64_t nnz, int64_t tiles, int2 *part)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > tiles) return;
+    const int64_t d = t * kMpTile < n + nnz ? t * kMpTile : n + nnz;
+    int64_t x, y;
+    mp_search(row_ptr, n, nnz, d, x, y);
+    part[t] = make_int2((int)x, (int)y);
+}
+
+struct KV {
+    int32_t k;
+    float v;
+};
+
+__global__ void __launch_bounds__(kMpBlock) k_mp_spmv(
+    const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+    const float *__restrict__ val, const float *__restrict__ x, float *__restrict__ y, int64_t n,
+    int64_t nnz, const int2 *__restrict__ part, int32_t *__restrict__ carry_row,
+    float *__restrict__ carry_val)
+{
+    __shared__ int32_t s_end[kMpTile + 1];     // row ends of the tile's rows, relative to y0
+    __shared__ float s_prod[kMpTile];          // products of the tile's nonzeros
+    __shared__ KV s_warp[kMpBlock / 32];
+    const int64_t tile = blockIdx.x;
+    const int2 p0 = part[tile], p1 = part[tile + 1];
+    const int x0 = p0.x, y0 = p0.y;
+    const int nrows = p1.x - p0.x, nnzt = p1.y - p0.y;
+    for (int i = threadIdx.x; i < nrows; i += kMpBlock)
+        s_end[i] = (int32_t)(__ldg(row_ptr + x0 + 1 + i) - y0);
+    if (threadIdx.x == 0) s_end[nrows] = 0x7FFFFFFF;      // sentinel: no row end beyond
+#pragma unroll
+    for (int u = 0; u < kMpItems; ++u) {
+        const int j = u * kMpBlock + threadIdx.x;
+        if (j < nnzt) s_prod[j] = __ldcs(val + y0 + j) * __ldg(x + __ldcs(col + y0 + j));
+    }
+    __syncthreads();
+    // this thread's split inside the tile
+    const int dt = threadIdx.x * kMpItems < nrows + nnzt ? threadIdx.x * kMpItems : nrows + nnzt;
+    int lo = dt - nnzt > 0 ? dt - nnzt : 0, hi = dt < nrows ? dt : nrows;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (s_end[mid] <= dt - mid - 1) lo = mid + 1;
+        else hi = mid;
+    }
+    int xt = lo, yt = dt - lo;
+    const int first_row = xt;
+    float acc = 0.0f;
+    float first_val = 0.0f;         // partial of the first row end this thread consumes
+    int first_end = -1;             // that row (relative), or -1 if none
+    // consume kMpItems path items in order
+#pragma unroll
+    for (int i = 0; i < kMpItems; ++i) {
+        if (xt + yt >= nrows + nnzt) break;
+        if (yt < s_end[xt]) {
+            acc += s_prod[yt];
+            ++yt;
+        } else {
+            if (first_end < 0) { first_end = xt; first_val = acc; }
+            else y[x0 + xt] = acc;                 // row begun and ended in this thread
+            acc = 0.0f;
+            ++xt;
+        }
+    }
+    // segmented scan of the threads' trailing partials (row xt, value acc):
+    // carry_in(t) = partial of row first_row accumulated by earlier threads
+    KV mine = {xt, acc};
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    KV inc = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t k = __shfl_up_sync(kFull, inc.k, o);
+        const float v = __shfl_up_sync(kFull, inc.v, o);
+        if (lane >= o && k == inc.k) inc.v = v + inc.v;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        KV w = lane < kMpBlock / 32 ? s_warp[lane] : KV{-1, 0.0f};
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t k = __shfl_up_sync(kFull, w.k, o);
+            const float v = __shfl_up_sync(kFull, w.v, o);
+            if (lane >= o && k == w.k) w.v = v + w.v;
+        }
+        if (lane < kMpBlock / 32) s_warp[lane] = w;       // inclusive over warps
+    }
+    __syncthreads();
+    if (warp > 0) {
+        const KV pw = s_warp[warp - 1];
+        if (pw.k == inc.k) inc.v = pw.v + inc.v;
+    }
+    // carry into this thread: the inclusive value of thread t-1 if it ended on first_row
+    KV prev;
+    prev.k = __shfl_up_sync(kFull, inc.k, 1);
+    prev.v = __shfl_up_sync(kFull, inc.v, 1);
+    if (lane == 0) prev = warp > 0 ? s_warp[warp - 1] : KV{-1, 0.0f};
+    const float cin = (threadIdx.x > 0 && prev.k == first_row) ? prev.v : 0.0f;
+    if (first_end >= 0) y[x0 + first_end] = cin + first_val;
+    if (threadIdx.x == kMpBlock - 1) {
+        // the tile's trailing partial (row continues into the next tile)
+        carry_row[tile] = x0 + inc.k;
+        carry_val[tile] = inc.v;
+    }
+}
+
+// y[r] += the carries of the tiles that ended inside row r, in tile order.
+__global__ void __launch_bounds__(256) k_mp_fixup(const int32_t *__restrict__ carry_row,
+                                                  const float *__restrict__ carry_val,
+                                                  int64_t tiles, int64_t n, float *__restrict__ y)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tiles) return;
+    const int32_t r = carry_row[t];
+    if (t > 0 && carry_row[t - 1] == r) return;          // not the first tile of the run
+    if (r >= n) return;
+    float s = 0.0f;
+    for (int64_t u = t; u < tiles && carry_row[u] == r; ++u) s += carry_val[u];
+    y[r] = s + y[r];
+}
+
 template <int LPR>
 void launch_rows(const int64_t *row_ptr, const int32_t *col, const float *val, const float *x,
                  float *y, int64_t n_rows, uint32_t *cnt, uint32_t *list, uint32_t cap,
@@ -207,9 +363,25 @@ extern "C" boba_status_t boba_spmv_csr(const int64_t *row_ptr, const int32_t *co
     float *partial = reinterpret_cast<float *>(b + L.partial);
     const uint32_t cap = (uint32_t)L.cap;
 
+    const int tv = tuned_variant(kTuneSpmv, nnz);   // 0 auto, 1..4: LPR 4, 8, 16, 32, 5 merge path
+    if (tv == 5) {
+        int2 *part = reinterpret_cast<int2 *>(b + L.mp_part);
+        int32_t *crow = reinterpret_cast<int32_t *>(b + L.mp_crow);
+        float *cval = reinterpret_cast<float *>(b + L.mp_cval);
+        BOBA_TIMED("spmv.partition", stream,
+                   k_mp_partition<<<(unsigned)cdiv(L.mp_tiles + 1, 256), 256, 0, stream>>>(
+                       row_ptr, n_rows, nnz, L.mp_tiles, part));
+        BOBA_TIMED("spmv", stream,
+                   k_mp_spmv<<<(unsigned)L.mp_tiles, kMpBlock, 0, stream>>>(
+                       row_ptr, col, val, x, y, n_rows, nnz, part, crow, cval));
+        BOBA_TIMED("spmv.fixup", stream,
+                   k_mp_fixup<<<(unsigned)cdiv(L.mp_tiles, 256), 256, 0, stream>>>(
+                       crow, cval, L.mp_tiles, n_rows, y));
+        BOBA_LAUNCH_CHECK();
+        return BOBA_OK;
+    }
     BOBA_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t), stream));
     const double avg = (double)nnz / (double)n_rows;
-    const int tv = tuned_variant(kTuneSpmv, nnz);           // 0 auto, 1..4: LPR 4, 8, 16, 32
     if (tv == 1) launch_rows<4>(row_ptr, col, val, x, y, n_rows, cnt, list, cap, dev->status, stream);
     else if (tv == 2) launch_rows<8>(row_ptr, col, val, x, y, n_rows, cnt, list, cap, dev->status, stream);
     else if (tv == 3) launch_rows<16>(row_ptr, col, val, x, y, n_rows, cnt, list, cap, dev->status, stream);

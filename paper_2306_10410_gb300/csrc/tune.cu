@@ -22,7 +22,7 @@ namespace {
 
 constexpr int kClasses = 64;
 constexpr int kMaxDev = 64;
-constexpr int kVariants[kTuneKernels] = {6, 6, 2, 5};   // first, relabel, batched, spmv
+constexpr int kVariants[kTuneKernels] = {6, 6, 2, 6};   // first, relabel, batched, spmv
 const char *kNames[kTuneKernels] = {"first", "relabel", "batched", "spmv"};
 
 std::mutex g_tmu;

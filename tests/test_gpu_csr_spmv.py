@@ -147,3 +147,47 @@ def test_full_size_rmat24_csr_spmv(boba):
     np.testing.assert_array_equal(col.cpu().numpy(), ocol)
     np.testing.assert_array_equal(val.cpu().numpy().view(np.uint32), oval.view(np.uint32))
     check_spmv(boba, (rp, col, val), (orp, ocol, oval), synth.uniform_f32(w.n, seed=w.seed))
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("case", ["rmat14", "hubs", "empty_rows", "one_row", "no_edges"])
+def test_spmv_variants(boba, variant, case):
+    """Every SpMV variant (lanes per row 4..32, merge path) within the fp32 bound,
+    deterministic run to run; hub rows crossing many merge-path tiles."""
+    rng = np.random.default_rng(9)
+    if case == "rmat14":
+        w = synth.RMAT14
+        I, J = w.generate()
+        n = w.n
+    elif case == "hubs":
+        n = 3000
+        I = rng.integers(0, n, 400_000).astype(np.int32)
+        J = np.where(rng.random(400_000) < 0.5, 17, rng.integers(0, n, 400_000)).astype(np.int32)
+    elif case == "empty_rows":                      # most rows empty, trailing empty rows
+        n = 100_000
+        I = rng.integers(0, n, 20_000).astype(np.int32)
+        J = rng.integers(0, 5_000, 20_000).astype(np.int32)
+    elif case == "one_row":
+        n = 1
+        I = np.zeros(70_000, np.int32)
+        J = np.zeros(70_000, np.int32)
+    else:
+        n = 777
+        I = np.zeros(0, np.int32)
+        J = np.zeros(0, np.int32)
+    rp, col, val = boba.coo_to_csr(dev(I), dev(J), n)
+    x = dev(synth.uniform_f32(n, seed=12))
+    boba.load().boba_tune_set(boba.TUNE_SPMV, col.numel(), variant)
+    try:
+        y1 = boba.spmv(rp, col, val, x)
+        y2 = boba.spmv(rp, col, val, x)
+        boba.stream_status()
+    finally:
+        boba.load().boba_tune_set(boba.TUNE_SPMV, col.numel(), -1)
+    assert torch.equal(y1, y2)
+    orp, ocol, oval = oracle.coo_to_csr(I, J, n)
+    y64 = oracle.spmv_f64(orp, ocol, oval, x.cpu().numpy())
+    y32 = y1.cpu().numpy().astype(np.float64)
+    nrm = np.linalg.norm(y64)
+    err = np.linalg.norm(y32 - y64) / nrm if nrm > 0 else np.linalg.norm(y32)
+    assert err <= SPMV_RTOL, err
