@@ -224,7 +224,16 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
 
     tuning = None
-    if args.tune:
+    if args.tune_spec:
+        # fixed variants (reproducible profiling): "first=5,relabel=3,spmv=5"
+        fam = {"first": boba.TUNE_FIRST, "relabel": boba.TUNE_RELABEL, "spmv": boba.TUNE_SPMV}
+        tuning = {}
+        for item in args.tune_spec.split(","):
+            k, v = item.split("=")
+            size = m
+            boba.load().boba_tune_set(fam[k], size, int(v))
+            tuning[k] = int(v)
+    elif args.tune:
         # autotune launch shapes on this workload (every variant checked bit-identical)
         tuning = boba.tune_reorder(src, dst, n, reps=3)
         if have_csr:
@@ -605,6 +614,8 @@ def main():
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--tune", type=int, default=1,
                     help="1: autotune launch variants on the workload before timing")
+    ap.add_argument("--tune-spec", default="",
+                    help="set variants instead of tuning, e.g. first=5,relabel=3,spmv=5")
     ap.add_argument("--serve", type=int, default=1,
                     help="1: also run the serving workload (Poisson requests, HBM budget)")
     ap.add_argument("--serve-requests", type=int, default=400)
