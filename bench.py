@@ -386,6 +386,12 @@ def compare_orders(args, boba, torch, dev, stream, src, dst, so, do, m, n, row_p
         out[name] = {"csr_ms": round(statistics.median(t_csr), 4), "spmv_ms": round(ms, 4),
                      "spmv_gbs": round(spmv_bytes / (ms * 1e-3) / 1e9, 1)}
     out["spmv_speedup_boba_vs_random"] = round(out["random"]["spmv_ms"] / out["boba"]["spmv_ms"], 3)
+    # NBR spatial-locality metric (Sec. 5.2) of the two CSRs, lines of 32 IDs
+    for name, (s_, d_) in (("random", (src, dst)), ("boba", (so, do))):
+        boba.check(boba.boba_coo_to_csr(s_, d_, m, n, row_ptr, col, val, ws_c, ws_c.numel(),
+                                        stream), "csr")
+        v, cnt = boba.nbr(row_ptr, col, ids_per_line=32)
+        out[name]["nbr32"] = round(v, 5)
     out["csr_speedup_boba_vs_random"] = round(out["random"]["csr_ms"] / out["boba"]["csr_ms"], 3)
     out["spmv_bytes_per_launch"] = spmv_bytes
     return out

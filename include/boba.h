@@ -332,6 +332,22 @@ boba_status_t boba_spmv_csr(const int64_t *row_ptr, const int32_t *col, const fl
 
 size_t boba_spmv_workspace_bytes(int64_t n_rows, int64_t nnz);
 
+/*
+ * boba_nbr -- the NBR spatial-locality metric of Sec. 5.2 over the rows of a
+ * CSR: the mean, over rows with at least one entry, of
+ * (distinct ids_per_line-wide lines spanned by the row's distinct column IDs)
+ * / (number of distinct column IDs).  Lower is better; a row whose
+ * neighbours share one line scores 1/|N(v)|.  Column IDs must be < n_rows
+ * (square matrix).  Synchronous: writes the metric to *nbr_out and the number
+ * of rows counted to *rows_counted (HOST pointers; the latter nullable).
+ * ws: scratch of boba_nbr_workspace_bytes(n_rows, nnz) bytes (device).
+ */
+boba_status_t boba_nbr(const int64_t *row_ptr, const int32_t *col, int64_t n_rows, int64_t nnz,
+                       int64_t ids_per_line, double *nbr_out, int64_t *rows_counted, void *ws,
+                       size_t ws_bytes, void *stream);
+
+size_t boba_nbr_workspace_bytes(int64_t n_rows, int64_t nnz);
+
 /* ------------------------------------------------------------------------
  * Status
  * ------------------------------------------------------------------------ */

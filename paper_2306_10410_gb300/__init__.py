@@ -17,7 +17,7 @@ __all__ = [
     "boba_reorder", "boba_reorder_ex", "boba_reorder_workspace_bytes", "boba_reorder_static", "boba_reorder_batched",
     "boba_reorder_batched_workspace_bytes", "boba_batched_set_mode", "boba_coo_to_csr", "boba_coo_to_csr_workspace_bytes",
     "boba_spmv_csr", "boba_spmv_workspace_bytes", "boba_stream_status", "boba_status_string",
-    "Workspace", "kernel_timing", "tune_reorder", "tune_batched", "tune_spmv", "tune_save",
+    "Workspace", "kernel_timing", "nbr", "tune_reorder", "tune_batched", "tune_spmv", "tune_save",
     "tune_load", "tune_reset", "TUNE_FIRST", "TUNE_RELABEL", "TUNE_BATCHED", "TUNE_SPMV",
 ]
 
@@ -317,3 +317,15 @@ def tune_load(path):
 
 def tune_reset():
     load().boba_tune_reset()
+
+
+def nbr(row_ptr, col, *, ids_per_line=32, ws=None, stream=None):
+    """(NBR, rows counted) of a CSR on the GPU (Sec. 5.2)."""
+    import ctypes
+    n_rows, nnz = row_ptr.numel() - 1, col.numel()
+    buf = _ws(ws, load().boba_nbr_workspace_bytes(n_rows, nnz), row_ptr.device)
+    out = ctypes.c_double(0.0)
+    cnt = ctypes.c_int64(0)
+    check(load().boba_nbr(_p(row_ptr), _p(col), n_rows, nnz, ids_per_line, ctypes.byref(out),
+                          ctypes.byref(cnt), _p(buf), buf.numel(), _s(stream)), "boba_nbr")
+    return out.value, cnt.value

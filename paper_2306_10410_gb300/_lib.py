@@ -46,6 +46,8 @@ SIGNATURES = {
     "boba_coo_to_csr_workspace_bytes": (_SZ, [_I64, _I64]),
     "boba_spmv_csr": (_ST, [_P, _P, _P, _P, _P, _I64, _I64, _P, _SZ, _P]),
     "boba_spmv_workspace_bytes": (_SZ, [_I64, _I64]),
+    "boba_nbr": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _SZ, _P]),
+    "boba_nbr_workspace_bytes": (_SZ, [_I64, _I64]),
     "boba_stream_status": (_ST, [_P]),
     "boba_status_string": (ctypes.c_char_p, [_ST]),
     "boba_version": (ctypes.c_char_p, []),

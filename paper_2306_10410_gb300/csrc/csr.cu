@@ -125,7 +125,7 @@ template <int BLOCK, int ITEMS>
 __global__ void __launch_bounds__(BLOCK) k_csr_pass(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t m, int p, const uint32_t *__restrict__ dstart,
-    uint64_t *status_lb, uint32_t *counters, uint32_t *status)
+    uint64_t *status_lb, uint32_t *counters, uint32_t *status, int digit)
 {
     constexpr int TILE = BLOCK * ITEMS;
     constexpr int WARPS = BLOCK / 32;
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(BLOCK) k_csr_pass(
     __syncthreads();
     const int64_t tile = s_tile;
     const int64_t t0 = tile * TILE;
-    const int shift = 8 * p;
+    const int shift = 8 * digit;
 
     // load: item (warp, k, lane) is tile index warp*WARP_ITEMS + k*32 + lane, so
     // the k-major / lane-minor processing order of a warp is the input order
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(BLOCK) k_csr_pass(
         uint64_t *st = status_lb + tile * 256 + d;
         if (tile == 0) {
             st_relaxed_u64(st, pass_flag(p, true) | cnt);
-            s_base[d] = dstart[p * 256 + d];
+            s_base[d] = dstart[digit * 256 + d];
         } else {
             st_relaxed_u64(st, pass_flag(p, false) | cnt);
             const uint64_t fa = pass_flag(p, false), fp = pass_flag(p, true);
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(BLOCK) k_csr_pass(
                 }
             }
             st_relaxed_u64(st, fp | ((excl + cnt) & kPassValMask));
-            s_base[d] = dstart[p * 256 + d] + (uint32_t)excl;
+            s_base[d] = dstart[digit * 256 + d] + (uint32_t)excl;
         }
     }
     __syncthreads();
@@ -328,10 +328,231 @@ __global__ void k_rowptr_zero(int64_t *row_ptr, int64_t n)
         row_ptr[v] = 0;
 }
 
+// ---------------------------------------------------------------------------
+// NBR locality metric (Sec. 5.2): for each row with a non-empty neighbour
+// set N(v), lines(N(v)) / |N(v)| with N(v) the distinct column IDs of the row
+// and lines the distinct ids_per_line-wide blocks of IDs they fall in; NBR is
+// the mean over those rows.  The columns of every row are sorted by two
+// stable radix sorts (by column, then by row), after which distinct values
+// and distinct lines are counted by comparing neighbours.
+// ---------------------------------------------------------------------------
+
+// Digit histograms (8-bit digits 0 .. digits-1) of a key array.
+__global__ void __launch_bounds__(256) k_digit_hist(const uint32_t *__restrict__ keys, int64_t m,
+                                                    int digits, uint32_t *hist)
+{
+    __shared__ uint32_t sh[kMaxPasses * 256];
+    for (int i = threadIdx.x; i < digits * 256; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = __ldcs(keys + e);
+        for (int d = 0; d < digits; ++d) atomicAdd(&sh[d * 256 + ((k >> (8 * d)) & 255u)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < digits * 256; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// rows[p] = r for every entry p of row r (a warp per row).
+__global__ void __launch_bounds__(256) k_expand_rows(const int64_t *__restrict__ row_ptr,
+                                                     int64_t n_rows, uint32_t *__restrict__ rows)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w; r < n_rows; r += nw) {
+        const int64_t b = row_ptr[r], e = row_ptr[r + 1];
+        for (int64_t p = b + lane; p < e; p += 32) rows[p] = (uint32_t)r;
+    }
+}
+
+// Per block: sum of lines/distinct over its rows (fixed order) and the count
+// of non-empty rows.  A warp per row; rows go to warps round-robin.
+__global__ void __launch_bounds__(256) k_nbr_rows(const int64_t *__restrict__ row_ptr,
+                                                  const uint32_t *__restrict__ scol, int64_t n_rows,
+                                                  uint32_t line, double *__restrict__ bsum,
+                                                  unsigned long long *__restrict__ bcnt)
+{
+    __shared__ double s_sum[8];
+    __shared__ unsigned long long s_cnt[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t w = (int64_t)blockIdx.x * 8 + warp;
+    const int64_t nw = (int64_t)gridDim.x * 8;
+    double sum = 0.0;
+    unsigned long long cnt = 0;
+    for (int64_t r = w; r < n_rows; r += nw) {
+        const int64_t b = row_ptr[r], e = row_ptr[r + 1];
+        if (e == b) continue;
+        uint32_t distinct = 0, lines = 0;
+        for (int64_t p = b + lane; p < e; p += 32) {
+            const uint32_t c = scol[p];
+            const bool first = p == b;
+            const uint32_t pc = first ? 0u : scol[p - 1];
+            distinct += (first || c != pc) ? 1u : 0u;
+            lines += (first || c / line != pc / line) ? 1u : 0u;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            distinct += __shfl_xor_sync(kFull, distinct, o);
+            lines += __shfl_xor_sync(kFull, lines, o);
+        }
+        sum += (double)lines / (double)distinct;          // same value in every lane
+        ++cnt;
+    }
+    if (lane == 0) { s_sum[warp] = sum; s_cnt[warp] = cnt; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        unsigned long long c = 0;
+        for (int i = 0; i < 8; ++i) { t += s_sum[i]; c += s_cnt[i]; }
+        bsum[blockIdx.x] = t;
+        bcnt[blockIdx.x] = c;
+    }
+}
+
+__global__ void k_nbr_final(const double *bsum, const unsigned long long *bcnt, int blocks,
+                            double *out_sum, unsigned long long *out_cnt)
+{
+    double t = 0.0;
+    unsigned long long c = 0;
+    for (int i = 0; i < blocks; ++i) { t += bsum[i]; c += bcnt[i]; }
+    *out_sum = t;
+    *out_cnt = c;
+}
+
+constexpr int kNbrBlocks = 1216;       // fixed, so the reduction order never changes
+
+struct NbrLayout {
+    int passes;
+    int64_t tiles;
+    size_t rows, kA, vA, kB, vB, hist1, hist2, status, counters, zero_begin, zero_end, dst1, dst2,
+        bsum, bcnt, out, total;
+};
+
+bool nbr_layout(int64_t n_rows, int64_t nnz, NbrLayout &L)
+{
+    if (n_rows < 0 || nnz < 0 || n_rows > kMaxSize || nnz > kMaxSize) return false;
+    int bits = 1;
+    while (bits < 31 && (1ll << bits) < n_rows) bits++;
+    L.passes = (bits + 7) / 8;
+    L.tiles = cdiv(nnz > 0 ? nnz : 1, kPassTile);
+    const size_t mm = (size_t)(nnz > 0 ? nnz : 1) * 4;
+    Carve c;
+    L.rows = c.take(mm);
+    L.kA = c.take(mm);
+    L.vA = c.take(mm);
+    L.kB = c.take(mm);
+    L.vB = c.take(mm);
+    L.zero_begin = c.off;
+    L.hist1 = c.take(kMaxPasses * 256 * 4);
+    L.hist2 = c.take(kMaxPasses * 256 * 4);
+    L.status = c.take((size_t)L.tiles * 256 * 8);
+    L.counters = c.take(kNumCtr * 4);
+    L.zero_end = c.off;
+    L.dst1 = c.take(kMaxPasses * 256 * 4);
+    L.dst2 = c.take(kMaxPasses * 256 * 4);
+    L.bsum = c.take(kNbrBlocks * 8);
+    L.bcnt = c.take(kNbrBlocks * 8);
+    L.out = c.take(16);
+    L.total = c.off;
+    return true;
+}
+
 }  // namespace
 }  // namespace boba
 
 using namespace boba;
+
+extern "C" size_t boba_nbr_workspace_bytes(int64_t n_rows, int64_t nnz)
+{
+    NbrLayout L;
+    if (!nbr_layout(n_rows, nnz, L)) return 0;
+    return L.total;
+}
+
+extern "C" boba_status_t boba_nbr(const int64_t *row_ptr, const int32_t *col, int64_t n_rows,
+                                  int64_t nnz, int64_t ids_per_line, double *nbr_out,
+                                  int64_t *rows_counted, void *ws, size_t ws_bytes, void *stream_)
+{
+    if (n_rows < 0 || nnz < 0 || ids_per_line < 1 || ids_per_line > 0x7FFFFFFF)
+        return BOBA_ERR_INVALID_ARG;
+    if (n_rows > kMaxSize || nnz > kMaxSize) return BOBA_ERR_TOO_LARGE;
+    if (nbr_out == nullptr) return BOBA_ERR_INVALID_ARG;
+    if (n_rows == 0 || nnz == 0) {
+        *nbr_out = 0.0;
+        if (rows_counted) *rows_counted = 0;
+        return BOBA_OK;
+    }
+    if (row_ptr == nullptr || col == nullptr) return BOBA_ERR_INVALID_ARG;
+    NbrLayout L;
+    nbr_layout(n_rows, nnz, L);
+    if (ws == nullptr || ws_bytes < L.total || !aligned256(ws)) return BOBA_ERR_WORKSPACE;
+    const DeviceInfo *dev = device_info();
+    if (!dev) return BOBA_ERR_CUDA;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    char *b = static_cast<char *>(ws);
+    auto U = [&](size_t off) { return reinterpret_cast<uint32_t *>(b + off); };
+    uint64_t *lb = reinterpret_cast<uint64_t *>(b + L.status);
+    const int64_t zero16 = (int64_t)(L.zero_end - L.zero_begin) / 16;
+    const int gz = persistent_grid((const void *)k_zero, 256, cdiv(zero16, 256));
+    BOBA_TIMED("nbr", stream, k_zero<<<gz, 256, 0, stream>>>(reinterpret_cast<uint4 *>(b + L.zero_begin), zero16));
+    const int gr = persistent_grid((const void *)k_expand_rows, 256, cdiv(n_rows * 32, 256));
+    BOBA_TIMED("nbr", stream, k_expand_rows<<<gr, 256, 0, stream>>>(row_ptr, n_rows, U(L.rows)));
+    const int gh = persistent_grid((const void *)k_digit_hist, 256, cdiv(nnz, 256));
+    BOBA_TIMED("nbr", stream,
+               k_digit_hist<<<gh, 256, 0, stream>>>(reinterpret_cast<const uint32_t *>(col), nnz,
+                                                    L.passes, U(L.hist1)));
+    BOBA_TIMED("nbr", stream, k_digit_hist<<<gh, 256, 0, stream>>>(U(L.rows), nnz, L.passes, U(L.hist2)));
+    BOBA_TIMED("nbr", stream, k_csr_digits<<<1, 256, 0, stream>>>(U(L.hist1), U(L.dst1), L.passes));
+    BOBA_TIMED("nbr", stream, k_csr_digits<<<1, 256, 0, stream>>>(U(L.hist2), U(L.dst2), L.passes));
+    // sort 1: by column (values: rows)
+    const uint32_t *kin = reinterpret_cast<const uint32_t *>(col), *vin = U(L.rows);
+    for (int p = 0; p < L.passes; ++p) {
+        uint32_t *ko = (p & 1) ? U(L.kB) : U(L.kA), *vo = (p & 1) ? U(L.vB) : U(L.vA);
+        BOBA_TIMED("nbr", stream,
+                   k_csr_pass<kPassBlock, kPassItems><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
+                       kin, vin, ko, vo, nnz, p, U(L.dst1), lb, U(L.counters), dev->status, p));
+        kin = ko;
+        vin = vo;
+    }
+    // sort 2: by row (values: columns), stable, so columns stay sorted in a row
+    BOBA_TIMED("nbr", stream, k_zero<<<gz, 256, 0, stream>>>(reinterpret_cast<uint4 *>(b + L.status),
+                                                             (int64_t)(L.zero_end - L.status) / 16));
+    // inputs of sort 2: rows (the values of sort 1) as keys, columns as values;
+    // outputs alternate between two free buffers and the two input buffers
+    uint32_t *rbuf = const_cast<uint32_t *>(vin), *cbuf = const_cast<uint32_t *>(kin);
+    uint32_t *fb[2];
+    int nf = 0;
+    for (uint32_t *q : {U(L.rows), U(L.kA), U(L.vA), U(L.kB), U(L.vB)})
+        if (q != rbuf && q != cbuf && nf < 2) fb[nf++] = q;
+    kin = rbuf;
+    vin = cbuf;
+    for (int p = 0; p < L.passes; ++p) {
+        uint32_t *ko = (p & 1) ? rbuf : fb[0], *vo = (p & 1) ? cbuf : fb[1];
+        BOBA_TIMED("nbr", stream,
+                   k_csr_pass<kPassBlock, kPassItems><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
+                       kin, vin, ko, vo, nnz, p, U(L.dst2), lb, U(L.counters), dev->status, p));
+        kin = ko;
+        vin = vo;
+    }
+    double *bsum = reinterpret_cast<double *>(b + L.bsum);
+    unsigned long long *bcnt = reinterpret_cast<unsigned long long *>(b + L.bcnt);
+    BOBA_TIMED("nbr", stream,
+               k_nbr_rows<<<kNbrBlocks, 256, 0, stream>>>(row_ptr, vin, n_rows,
+                                                          (uint32_t)ids_per_line, bsum, bcnt));
+    double *dsum = reinterpret_cast<double *>(b + L.out);
+    unsigned long long *dcnt = reinterpret_cast<unsigned long long *>(b + L.out + 8);
+    BOBA_TIMED("nbr", stream, k_nbr_final<<<1, 1, 0, stream>>>(bsum, bcnt, kNbrBlocks, dsum, dcnt));
+    double hs = 0.0;
+    unsigned long long hc = 0;
+    BOBA_CUDA_TRY(cudaMemcpyAsync(&hs, dsum, 8, cudaMemcpyDeviceToHost, stream));
+    BOBA_CUDA_TRY(cudaMemcpyAsync(&hc, dcnt, 8, cudaMemcpyDeviceToHost, stream));
+    BOBA_CUDA_TRY(cudaStreamSynchronize(stream));
+    *nbr_out = hc ? hs / (double)hc : 0.0;
+    if (rows_counted) *rows_counted = (int64_t)hc;
+    return BOBA_OK;
+}
 
 extern "C" size_t boba_coo_to_csr_workspace_bytes(int64_t m, int64_t n)
 {
@@ -395,7 +616,7 @@ extern "C" boba_status_t boba_coo_to_csr(const int32_t *src, const int32_t *dst,
         uint32_t *vo = last ? reinterpret_cast<uint32_t *>(col_out) : ((p & 1) ? vB : vA);
         BOBA_TIMED("csr.pass", stream,
                    k_csr_pass<kPassBlock, kPassItems><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
-                       kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status));
+                       kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status, p));
         kin = ko;
         vin = vo;
     }

@@ -1,0 +1,62 @@
+"""GPU NBR metric (Sec. 5.2) against the oracle; BOBA lowers it on R-MAT."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def boba():
+    import paper_2306_10410_gb300 as b
+    b.load()
+    return b
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_hand_example(boba):
+    # row 0: {0,1,2} -> 1/3 ; row 1: {0, 32} -> 1 ; row 2: {5, 5} -> 1 ; row 3 empty
+    rp = np.array([0, 3, 5, 7, 7], np.int64)
+    col = np.array([2, 0, 1, 32, 0, 5, 5], np.int32)
+    v, c = boba.nbr(dev(rp), dev(col), ids_per_line=32)
+    assert c == 3 and abs(v - (1 / 3 + 1 + 1) / 3) < 1e-15
+
+
+@pytest.mark.parametrize("line", [1, 8, 32])
+@pytest.mark.parametrize("order", ["random", "boba"])
+def test_matches_oracle(boba, line, order):
+    w = synth.RMAT14
+    I, J = w.generate()
+    if order == "boba":
+        _, I, J = oracle.reorder(I, J, w.n)
+    rp, col, _ = oracle.coo_to_csr(I, J, w.n)
+    v, c = boba.nbr(dev(rp), dev(col), ids_per_line=line)
+    ov, oc = oracle.nbr(rp, col, line)
+    assert c == oc
+    assert abs(v - ov) <= 1e-12 * max(1.0, ov)
+
+
+def test_long_rows_and_wide_ids(boba):
+    rng = np.random.default_rng(4)
+    n = 300_000
+    I = rng.integers(0, n, 500_000).astype(np.int32)
+    J = np.where(rng.random(500_000) < 0.3, 11, rng.integers(0, n, 500_000)).astype(np.int32)
+    rp, col, _ = oracle.coo_to_csr(I, J, n)
+    v, c = boba.nbr(dev(rp), dev(col))
+    ov, oc = oracle.nbr(rp, col, 32)
+    assert c == oc and abs(v - ov) <= 1e-12
+
+
+def test_boba_improves_locality_on_rmat(boba):
+    I, J = synth.rmat(18, 1 << 22, seed=8)
+    n = 1 << 18
+    _, Io, Jo = oracle.reorder(I, J, n)
+    vr, _ = boba.nbr(*[dev(a) for a in oracle.coo_to_csr(I, J, n)[:2]])
+    vb, _ = boba.nbr(*[dev(a) for a in oracle.coo_to_csr(Io, Jo, n)[:2]])
+    assert vb < vr
