@@ -386,6 +386,42 @@ def compare_orders(args, boba, torch, dev, stream, src, dst, so, do, m, n, row_p
         out[name] = {"csr_ms": round(statistics.median(t_csr), 4), "spmv_ms": round(ms, 4),
                      "spmv_gbs": round(spmv_bytes / (ms * 1e-3) / 1e9, 1)}
     out["spmv_speedup_boba_vs_random"] = round(out["random"]["spmv_ms"] / out["boba"]["spmv_ms"], 3)
+    # Sec. 5.6: sort (or bin) the randomly ordered edges by destination, then BOBA
+    s2, d2 = torch.empty_like(src), torch.empty_like(dst)
+    s3, d3 = torch.empty_like(src), torch.empty_like(dst)
+    perm2 = torch.empty(n, dtype=torch.int32, device=dev)
+    ws_sort = torch.empty(boba.boba_sort_by_dst_workspace_bytes(m, n), dtype=torch.uint8,
+                          device=dev)
+    ws_r2 = torch.empty(boba.boba_reorder_workspace_bytes(m, n), dtype=torch.uint8, device=dev)
+    for name, top in (("boba_dst_sorted", 0), ("boba_dst_binned", 1)):
+        ts, tr, tsp = [], [], []
+        for rep in range(4):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            flush.zero_()
+            ev[0].record(stream)
+            boba.check(boba.boba_sort_by_dst(src, dst, m, n, s2, d2, top, ws_sort,
+                                             ws_sort.numel(), stream), "sort")
+            ev[1].record(stream)
+            boba.check(boba.boba_reorder_ex(s2, d2, m, n, perm2, s3, d3, None, ws_r2,
+                                            ws_r2.numel(), stream), "reorder")
+            ev[2].record(stream)
+            boba.check(boba.boba_coo_to_csr(s3, d3, m, n, row_ptr, col, val, ws_c, ws_c.numel(),
+                                            stream), "csr")
+            for _ in range(args.spmv_iters):
+                boba.check(boba.boba_spmv_csr(row_ptr, col, val, x, y, n, m, ws_s, ws_s.numel(),
+                                              stream), "spmv")
+            ev[3].record(stream)
+            torch.cuda.synchronize(dev)
+            if rep:
+                ts.append(ev[0].elapsed_time(ev[1]))
+                tr.append(ev[1].elapsed_time(ev[2]))
+                tsp.append(ev[2].elapsed_time(ev[3]))
+        v, _ = boba.nbr(row_ptr, col, ids_per_line=32)
+        out[name] = {"sort_ms": round(statistics.median(ts), 4),
+                     "reorder_ms": round(statistics.median(tr), 4),
+                     "csr_plus_spmv_ms": round(statistics.median(tsp), 4), "nbr32": round(v, 5)}
+    del s2, d2, s3, d3, ws_sort, ws_r2
+    boba.stream_status(stream)
     # NBR spatial-locality metric (Sec. 5.2) of the two CSRs, lines of 32 IDs
     for name, (s_, d_) in (("random", (src, dst)), ("boba", (so, do))):
         boba.check(boba.boba_coo_to_csr(s_, d_, m, n, row_ptr, col, val, ws_c, ws_c.numel(),

@@ -333,6 +333,21 @@ boba_status_t boba_spmv_csr(const int64_t *row_ptr, const int32_t *col, const fl
 size_t boba_spmv_workspace_bytes(int64_t n_rows, int64_t nnz);
 
 /*
+ * boba_sort_by_dst -- reorders the edges of a COO stably by destination
+ * (top_digit_only = 0: a full sort; != 0: only by the top 8 bits of the
+ * destination, a binning pass).  Sec. 5.6 suggests sorting or binning an edge
+ * list that arrives in random order by destination before running BOBA;
+ * sources that share a destination then sit together in I and get nearby
+ * labels.  src_out/dst_out must not alias the inputs.
+ *   ws  scratch of boba_sort_by_dst_workspace_bytes(m, n) bytes (device)
+ */
+boba_status_t boba_sort_by_dst(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                               int32_t *src_out, int32_t *dst_out, int top_digit_only,
+                               void *ws, size_t ws_bytes, void *stream);
+
+size_t boba_sort_by_dst_workspace_bytes(int64_t m, int64_t n);
+
+/*
  * boba_nbr -- the NBR spatial-locality metric of Sec. 5.2 over the rows of a
  * CSR: the mean, over rows with at least one entry, of
  * (distinct ids_per_line-wide lines spanned by the row's distinct column IDs)

@@ -18,6 +18,8 @@ of the paper it follows:
                           fp32(1/outdeg(source))
 * :func:`spmv_f64`     -- Algorithm 3 in fp64
 * :func:`nbr`          -- the NBR line metric (Sec. 5.2)
+* :func:`sort_by_dst`  -- the edge list stably sorted or binned by destination,
+                          the remedy for random edge order (Sec. 5.6)
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (paper worked examples, brute force, closed forms, invariants).
@@ -185,3 +187,18 @@ def nbr(row_ptr, col, ids_per_line: int = 32):
     if counted.value < 0:
         raise OracleError("nbr: out of memory")
     return float(v), int(counted.value)
+
+
+def sort_by_dst(I, J, n: int, top_digit_only: bool = False):
+    """Edges stably sorted by destination (Sec. 5.6); or, with top_digit_only,
+    stably binned by the top 8 bits of the ceil(log2 n)-bit destination."""
+    I, J = _i32(I), _i32(J)
+    bits = 1
+    while bits < 31 and (1 << bits) < n:
+        bits += 1
+    passes = (bits + 7) // 8
+    key = J.astype(np.int64)
+    if top_digit_only:
+        key = (key >> (8 * (passes - 1))) & 255
+    order = np.argsort(key, kind="stable")
+    return I[order], J[order]

@@ -17,7 +17,7 @@ __all__ = [
     "boba_reorder", "boba_reorder_ex", "boba_reorder_workspace_bytes", "boba_reorder_static", "boba_reorder_batched",
     "boba_reorder_batched_workspace_bytes", "boba_batched_set_mode", "boba_coo_to_csr", "boba_coo_to_csr_workspace_bytes",
     "boba_spmv_csr", "boba_spmv_workspace_bytes", "boba_stream_status", "boba_status_string",
-    "Workspace", "kernel_timing", "nbr", "tune_reorder", "tune_batched", "tune_spmv", "tune_save",
+    "Workspace", "kernel_timing", "nbr", "sort_by_dst", "tune_reorder", "tune_batched", "tune_spmv", "tune_save",
     "tune_load", "tune_reset", "TUNE_FIRST", "TUNE_RELABEL", "TUNE_BATCHED", "TUNE_SPMV",
 ]
 
@@ -329,3 +329,14 @@ def nbr(row_ptr, col, *, ids_per_line=32, ws=None, stream=None):
     check(load().boba_nbr(_p(row_ptr), _p(col), n_rows, nnz, ids_per_line, ctypes.byref(out),
                           ctypes.byref(cnt), _p(buf), buf.numel(), _s(stream)), "boba_nbr")
     return out.value, cnt.value
+
+
+def sort_by_dst(src, dst, n, *, bin_only=False, src_out=None, dst_out=None, ws=None, stream=None):
+    """COO stably sorted (or binned by the top 8 bits) by destination: (src_out, dst_out)."""
+    m = src.numel()
+    src_out = torch.empty_like(src) if src_out is None else src_out
+    dst_out = torch.empty_like(dst) if dst_out is None else dst_out
+    buf = _ws(ws, load().boba_sort_by_dst_workspace_bytes(m, n), src.device)
+    check(load().boba_sort_by_dst(_p(src), _p(dst), m, n, _p(src_out), _p(dst_out), int(bin_only),
+                                  _p(buf), buf.numel(), _s(stream)), "boba_sort_by_dst")
+    return src_out, dst_out

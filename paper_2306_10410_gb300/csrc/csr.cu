@@ -554,6 +554,96 @@ extern "C" boba_status_t boba_nbr(const int64_t *row_ptr, const int32_t *col, in
     return BOBA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Stable sort (or binning) of a COO by destination, the remedy Sec. 5.6
+// suggests for edge lists in random order before running BOBA.
+// ---------------------------------------------------------------------------
+
+namespace boba {
+namespace {
+
+struct SortLayout {
+    int passes;
+    int64_t tiles;
+    size_t kA, vA, kB, vB, zero_begin, hist, status, counters, zero_end, dstart, total;
+};
+
+bool sort_layout(int64_t m, int64_t n, SortLayout &L)
+{
+    if (m < 0 || n < 0 || m > kMaxSize || n > kMaxSize) return false;
+    int bits = 1;
+    while (bits < 31 && (1ll << bits) < n) bits++;
+    L.passes = (bits + 7) / 8;
+    L.tiles = cdiv(m > 0 ? m : 1, kPassTile);
+    const size_t mm = (size_t)(m > 0 ? m : 1) * 4;
+    Carve c;
+    L.kA = c.take(mm);
+    L.vA = c.take(mm);
+    L.kB = c.take(mm);
+    L.vB = c.take(mm);
+    L.zero_begin = c.off;
+    L.hist = c.take(kMaxPasses * 256 * 4);
+    L.status = c.take((size_t)L.tiles * 256 * 8);
+    L.counters = c.take(kNumCtr * 4);
+    L.zero_end = c.off;
+    L.dstart = c.take(kMaxPasses * 256 * 4);
+    L.total = c.off;
+    return true;
+}
+
+}  // namespace
+}  // namespace boba
+
+extern "C" size_t boba_sort_by_dst_workspace_bytes(int64_t m, int64_t n)
+{
+    SortLayout L;
+    if (!sort_layout(m, n, L)) return 0;
+    return L.total;
+}
+
+extern "C" boba_status_t boba_sort_by_dst(const int32_t *src, const int32_t *dst, int64_t m,
+                                          int64_t n, int32_t *src_out, int32_t *dst_out,
+                                          int top_digit_only, void *ws, size_t ws_bytes,
+                                          void *stream_)
+{
+    if (m < 0 || n < 0) return BOBA_ERR_INVALID_ARG;
+    if (m > kMaxSize || n > kMaxSize) return BOBA_ERR_TOO_LARGE;
+    if (m == 0) return BOBA_OK;
+    if (!src || !dst || !src_out || !dst_out) return BOBA_ERR_INVALID_ARG;
+    SortLayout L;
+    sort_layout(m, n, L);
+    if (ws == nullptr || ws_bytes < L.total || !aligned256(ws)) return BOBA_ERR_WORKSPACE;
+    const DeviceInfo *dev = device_info();
+    if (!dev) return BOBA_ERR_CUDA;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    char *b = static_cast<char *>(ws);
+    auto U = [&](size_t off) { return reinterpret_cast<uint32_t *>(b + off); };
+    const int64_t zero16 = (int64_t)(L.zero_end - L.zero_begin) / 16;
+    const int gz = persistent_grid((const void *)k_zero, 256, cdiv(zero16, 256));
+    BOBA_TIMED("sort", stream, k_zero<<<gz, 256, 0, stream>>>(reinterpret_cast<uint4 *>(b + L.zero_begin), zero16));
+    const int gh = persistent_grid((const void *)k_digit_hist, 256, cdiv(m, 256));
+    BOBA_TIMED("sort", stream,
+               k_digit_hist<<<gh, 256, 0, stream>>>(reinterpret_cast<const uint32_t *>(dst), m,
+                                                    L.passes, U(L.hist)));
+    BOBA_TIMED("sort", stream, k_csr_digits<<<1, 256, 0, stream>>>(U(L.hist), U(L.dstart), L.passes));
+    const int d0 = top_digit_only ? L.passes - 1 : 0;
+    const uint32_t *kin = reinterpret_cast<const uint32_t *>(dst);
+    const uint32_t *vin = reinterpret_cast<const uint32_t *>(src);
+    for (int d = d0, p = 0; d < L.passes; ++d, ++p) {
+        const bool last = d == L.passes - 1;
+        uint32_t *ko = last ? reinterpret_cast<uint32_t *>(dst_out) : ((p & 1) ? U(L.kB) : U(L.kA));
+        uint32_t *vo = last ? reinterpret_cast<uint32_t *>(src_out) : ((p & 1) ? U(L.vB) : U(L.vA));
+        BOBA_TIMED("sort", stream,
+                   k_csr_pass<kPassBlock, kPassItems><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
+                       kin, vin, ko, vo, m, p, U(L.dstart), reinterpret_cast<uint64_t *>(b + L.status),
+                       U(L.counters), dev->status, d));
+        kin = ko;
+        vin = vo;
+    }
+    BOBA_LAUNCH_CHECK();
+    return BOBA_OK;
+}
+
 extern "C" size_t boba_coo_to_csr_workspace_bytes(int64_t m, int64_t n)
 {
     CsrLayout L;

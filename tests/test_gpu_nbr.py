@@ -60,3 +60,23 @@ def test_boba_improves_locality_on_rmat(boba):
     vr, _ = boba.nbr(*[dev(a) for a in oracle.coo_to_csr(I, J, n)[:2]])
     vb, _ = boba.nbr(*[dev(a) for a in oracle.coo_to_csr(Io, Jo, n)[:2]])
     assert vb < vr
+
+
+@pytest.mark.parametrize("bin_only", [False, True])
+def test_sort_by_dst_then_boba(boba, bin_only):
+    """Sec. 5.6: sorting (or binning) a randomly ordered edge list by destination
+    before BOBA.  The sort is bit-exact; afterwards BOBA lowers NBR below both
+    the random order and BOBA on the random order."""
+    I, J = synth.rmat(18, 1 << 22, seed=9)
+    n = 1 << 18
+    so, do = boba.sort_by_dst(dev(I), dev(J), n, bin_only=bin_only)
+    boba.stream_status()
+    oI, oJ = oracle.sort_by_dst(I, J, n, top_digit_only=bin_only)
+    np.testing.assert_array_equal(so.cpu().numpy(), oI)
+    np.testing.assert_array_equal(do.cpu().numpy(), oJ)
+    _, bI, bJ = oracle.reorder(oI, oJ, n)
+    _, rI, rJ = oracle.reorder(I, J, n)
+    v_sorted, _ = boba.nbr(*[dev(a) for a in oracle.coo_to_csr(bI, bJ, n)[:2]])
+    v_boba, _ = boba.nbr(*[dev(a) for a in oracle.coo_to_csr(rI, rJ, n)[:2]])
+    v_rand, _ = boba.nbr(*[dev(a) for a in oracle.coo_to_csr(I, J, n)[:2]])
+    assert v_sorted < v_boba < v_rand

@@ -297,3 +297,20 @@ def test_nbr_hand_and_brute():
         assert c == bc and abs(v - bv) < 1e-12
     v1, _ = oracle.nbr(rp, cl, 1)
     assert v1 == 1.0                                     # one ID per line: ratio is 1
+
+
+def test_sort_by_dst_pins():
+    """The full sort is the CSR's edge order; the binned order has non-decreasing
+    top digits and keeps input order within a bin (brute force)."""
+    I, J = synth.rmat(12, 30000, seed=13)
+    n = 1 << 12
+    Is, Js = oracle.sort_by_dst(I, J, n)
+    rp, col, _ = oracle.coo_to_csr(I, J, n)
+    assert np.array_equal(Is, col)
+    assert np.array_equal(Js, np.repeat(np.arange(n), np.diff(rp)))
+    Ib, Jb = oracle.sort_by_dst(I, J, n, top_digit_only=True)
+    top = lambda j: j >> 8                                  # 12-bit IDs: two digits
+    assert np.all(np.diff(top(Jb)) >= 0)
+    for d in range(0, 16, 5):
+        sel = top(J) == d
+        assert np.array_equal(Ib[top(Jb) == d], I[sel]) and np.array_equal(Jb[top(Jb) == d], J[sel])
