@@ -334,8 +334,9 @@ size_t boba_spmv_workspace_bytes(int64_t n_rows, int64_t nnz);
 
 /*
  * boba_sort_by_dst -- reorders the edges of a COO stably by destination
- * (top_digit_only = 0: a full sort; != 0: only by the top 8 bits of the
- * destination, a binning pass).  Sec. 5.6 suggests sorting or binning an edge
+ * (top_digit_only = 0: a full sort; != 0: only by the top 8 significant
+ * bits of the destination as a ceil(log2 n)-bit number -- 256 bins, one
+ * pass).  Sec. 5.6 suggests sorting or binning an edge
  * list that arrives in random order by destination before running BOBA;
  * sources that share a destination then sit together in I and get nearby
  * labels.  src_out/dst_out must not alias the inputs.

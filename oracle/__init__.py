@@ -196,9 +196,8 @@ def sort_by_dst(I, J, n: int, top_digit_only: bool = False):
     bits = 1
     while bits < 31 and (1 << bits) < n:
         bits += 1
-    passes = (bits + 7) // 8
     key = J.astype(np.int64)
     if top_digit_only:
-        key = (key >> (8 * (passes - 1))) & 255
+        key = (key >> max(0, bits - 8)) & 255
     order = np.argsort(key, kind="stable")
     return I[order], J[order]

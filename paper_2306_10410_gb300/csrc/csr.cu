@@ -125,7 +125,7 @@ template <int BLOCK, int ITEMS>
 __global__ void __launch_bounds__(BLOCK) k_csr_pass(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t m, int p, const uint32_t *__restrict__ dstart,
-    uint64_t *status_lb, uint32_t *counters, uint32_t *status, int digit)
+    uint64_t *status_lb, uint32_t *counters, uint32_t *status, int digit, int base_shift)
 {
     constexpr int TILE = BLOCK * ITEMS;
     constexpr int WARPS = BLOCK / 32;
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(BLOCK) k_csr_pass(
     __syncthreads();
     const int64_t tile = s_tile;
     const int64_t t0 = tile * TILE;
-    const int shift = 8 * digit;
+    const int shift = base_shift + 8 * digit;
 
     // load: item (warp, k, lane) is tile index warp*WARP_ITEMS + k*32 + lane, so
     // the k-major / lane-minor processing order of a warp is the input order
@@ -339,7 +339,7 @@ __global__ void k_rowptr_zero(int64_t *row_ptr, int64_t n)
 
 // Digit histograms (8-bit digits 0 .. digits-1) of a key array.
 __global__ void __launch_bounds__(256) k_digit_hist(const uint32_t *__restrict__ keys, int64_t m,
-                                                    int digits, uint32_t *hist)
+                                                    int digits, uint32_t *hist, int base_shift)
 {
     __shared__ uint32_t sh[kMaxPasses * 256];
     for (int i = threadIdx.x; i < digits * 256; i += blockDim.x) sh[i] = 0;
@@ -347,7 +347,8 @@ __global__ void __launch_bounds__(256) k_digit_hist(const uint32_t *__restrict__
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t k = __ldcs(keys + e);
-        for (int d = 0; d < digits; ++d) atomicAdd(&sh[d * 256 + ((k >> (8 * d)) & 255u)], 1u);
+        for (int d = 0; d < digits; ++d)
+            atomicAdd(&sh[d * 256 + ((k >> (base_shift + 8 * d)) & 255u)], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < digits * 256; i += blockDim.x)
@@ -502,8 +503,9 @@ extern "C" boba_status_t boba_nbr(const int64_t *row_ptr, const int32_t *col, in
     const int gh = persistent_grid((const void *)k_digit_hist, 256, cdiv(nnz, 256));
     BOBA_TIMED("nbr", stream,
                k_digit_hist<<<gh, 256, 0, stream>>>(reinterpret_cast<const uint32_t *>(col), nnz,
-                                                    L.passes, U(L.hist1)));
-    BOBA_TIMED("nbr", stream, k_digit_hist<<<gh, 256, 0, stream>>>(U(L.rows), nnz, L.passes, U(L.hist2)));
+                                                    L.passes, U(L.hist1), 0));
+    BOBA_TIMED("nbr", stream,
+               k_digit_hist<<<gh, 256, 0, stream>>>(U(L.rows), nnz, L.passes, U(L.hist2), 0));
     BOBA_TIMED("nbr", stream, k_csr_digits<<<1, 256, 0, stream>>>(U(L.hist1), U(L.dst1), L.passes));
     BOBA_TIMED("nbr", stream, k_csr_digits<<<1, 256, 0, stream>>>(U(L.hist2), U(L.dst2), L.passes));
     // sort 1: by column (values: rows)
@@ -512,7 +514,7 @@ extern "C" boba_status_t boba_nbr(const int64_t *row_ptr, const int32_t *col, in
         uint32_t *ko = (p & 1) ? U(L.kB) : U(L.kA), *vo = (p & 1) ? U(L.vB) : U(L.vA);
         BOBA_TIMED("nbr", stream,
                    k_csr_pass<kPassBlock, kPassItems><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
-                       kin, vin, ko, vo, nnz, p, U(L.dst1), lb, U(L.counters), dev->status, p));
+                       kin, vin, ko, vo, nnz, p, U(L.dst1), lb, U(L.counters), dev->status, p, 0));
         kin = ko;
         vin = vo;
     }
@@ -532,7 +534,7 @@ extern "C" boba_status_t boba_nbr(const int64_t *row_ptr, const int32_t *col, in
         uint32_t *ko = (p & 1) ? rbuf : fb[0], *vo = (p & 1) ? cbuf : fb[1];
         BOBA_TIMED("nbr", stream,
                    k_csr_pass<kPassBlock, kPassItems><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
-                       kin, vin, ko, vo, nnz, p, U(L.dst2), lb, U(L.counters), dev->status, p));
+                       kin, vin, ko, vo, nnz, p, U(L.dst2), lb, U(L.counters), dev->status, p, 0));
         kin = ko;
         vin = vo;
     }
@@ -563,7 +565,7 @@ namespace boba {
 namespace {
 
 struct SortLayout {
-    int passes;
+    int passes, bits;
     int64_t tiles;
     size_t kA, vA, kB, vB, zero_begin, hist, status, counters, zero_end, dstart, total;
 };
@@ -573,6 +575,7 @@ bool sort_layout(int64_t m, int64_t n, SortLayout &L)
     if (m < 0 || n < 0 || m > kMaxSize || n > kMaxSize) return false;
     int bits = 1;
     while (bits < 31 && (1ll << bits) < n) bits++;
+    L.bits = bits;
     L.passes = (bits + 7) / 8;
     L.tiles = cdiv(m > 0 ? m : 1, kPassTile);
     const size_t mm = (size_t)(m > 0 ? m : 1) * 4;
@@ -621,22 +624,25 @@ extern "C" boba_status_t boba_sort_by_dst(const int32_t *src, const int32_t *dst
     const int64_t zero16 = (int64_t)(L.zero_end - L.zero_begin) / 16;
     const int gz = persistent_grid((const void *)k_zero, 256, cdiv(zero16, 256));
     BOBA_TIMED("sort", stream, k_zero<<<gz, 256, 0, stream>>>(reinterpret_cast<uint4 *>(b + L.zero_begin), zero16));
+    // full sort: digits 0 .. passes-1 from bit 0; binning: one digit, the top 8
+    // significant bits of a ceil(log2 n)-bit ID
+    const int digits = top_digit_only ? 1 : L.passes;
+    const int base = top_digit_only ? (L.bits > 8 ? L.bits - 8 : 0) : 0;
     const int gh = persistent_grid((const void *)k_digit_hist, 256, cdiv(m, 256));
     BOBA_TIMED("sort", stream,
                k_digit_hist<<<gh, 256, 0, stream>>>(reinterpret_cast<const uint32_t *>(dst), m,
-                                                    L.passes, U(L.hist)));
-    BOBA_TIMED("sort", stream, k_csr_digits<<<1, 256, 0, stream>>>(U(L.hist), U(L.dstart), L.passes));
-    const int d0 = top_digit_only ? L.passes - 1 : 0;
+                                                    digits, U(L.hist), base));
+    BOBA_TIMED("sort", stream, k_csr_digits<<<1, 256, 0, stream>>>(U(L.hist), U(L.dstart), digits));
     const uint32_t *kin = reinterpret_cast<const uint32_t *>(dst);
     const uint32_t *vin = reinterpret_cast<const uint32_t *>(src);
-    for (int d = d0, p = 0; d < L.passes; ++d, ++p) {
-        const bool last = d == L.passes - 1;
+    for (int d = 0, p = 0; d < digits; ++d, ++p) {
+        const bool last = d == digits - 1;
         uint32_t *ko = last ? reinterpret_cast<uint32_t *>(dst_out) : ((p & 1) ? U(L.kB) : U(L.kA));
         uint32_t *vo = last ? reinterpret_cast<uint32_t *>(src_out) : ((p & 1) ? U(L.vB) : U(L.vA));
         BOBA_TIMED("sort", stream,
                    k_csr_pass<kPassBlock, kPassItems><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
                        kin, vin, ko, vo, m, p, U(L.dstart), reinterpret_cast<uint64_t *>(b + L.status),
-                       U(L.counters), dev->status, d));
+                       U(L.counters), dev->status, d, base));
         kin = ko;
         vin = vo;
     }
@@ -706,7 +712,7 @@ extern "C" boba_status_t boba_coo_to_csr(const int32_t *src, const int32_t *dst,
         uint32_t *vo = last ? reinterpret_cast<uint32_t *>(col_out) : ((p & 1) ? vB : vA);
         BOBA_TIMED("csr.pass", stream,
                    k_csr_pass<kPassBlock, kPassItems><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
-                       kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status, p));
+                       kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status, p, 0));
         kin = ko;
         vin = vo;
     }

@@ -309,8 +309,8 @@ def test_sort_by_dst_pins():
     assert np.array_equal(Is, col)
     assert np.array_equal(Js, np.repeat(np.arange(n), np.diff(rp)))
     Ib, Jb = oracle.sort_by_dst(I, J, n, top_digit_only=True)
-    top = lambda j: j >> 8                                  # 12-bit IDs: two digits
+    top = lambda j: j >> 4                                  # top 8 of 12 bits: 256 bins
     assert np.all(np.diff(top(Jb)) >= 0)
-    for d in range(0, 16, 5):
+    for d in range(0, 256, 37):
         sel = top(J) == d
         assert np.array_equal(Ib[top(Jb) == d], I[sel]) and np.array_equal(Jb[top(Jb) == d], J[sel])
