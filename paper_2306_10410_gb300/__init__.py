@@ -104,6 +104,75 @@ def boba_spmv_workspace_bytes(n_rows, nnz):
     return load().boba_spmv_workspace_bytes(n_rows, nnz)
 
 
+def boba_first_keys(src, dst, m_local, pos_src, pos_dst, n, key, init, stream=None):
+    return load().boba_first_keys(_p(src), _p(dst), m_local, pos_src, pos_dst, n, _p(key), init,
+                                  _s(stream))
+
+
+def boba_labels_workspace_bytes(m_total, n):
+    return load().boba_labels_workspace_bytes(m_total, n)
+
+
+def boba_labels_from_keys(key, m_total, n, perm_out, label_out, ws, ws_bytes, stream=None):
+    return load().boba_labels_from_keys(_p(key), m_total, n, _p(perm_out), _p(label_out), _p(ws),
+                                        ws_bytes, _s(stream))
+
+
+def boba_relabel(src, dst, m, n, label, src_out, dst_out, stream=None):
+    return load().boba_relabel(_p(src), _p(dst), m, n, _p(label), _p(src_out), _p(dst_out),
+                               _s(stream))
+
+
+def boba_sort_by_dst(src, dst, m, n, src_out, dst_out, top_digit_only, ws, ws_bytes, stream=None):
+    return load().boba_sort_by_dst(_p(src), _p(dst), m, n, _p(src_out), _p(dst_out),
+                                   int(top_digit_only), _p(ws), ws_bytes, _s(stream))
+
+
+def boba_sort_by_dst_workspace_bytes(m, n):
+    return load().boba_sort_by_dst_workspace_bytes(m, n)
+
+
+def boba_nbr(row_ptr, col, n_rows, nnz, ids_per_line, nbr_out, rows_counted, ws, ws_bytes,
+             stream=None):
+    """nbr_out / rows_counted are ctypes host objects (c_double / c_int64) passed by reference."""
+    import ctypes
+    return load().boba_nbr(_p(row_ptr), _p(col), n_rows, nnz, ids_per_line, ctypes.byref(nbr_out),
+                           None if rows_counted is None else ctypes.byref(rows_counted), _p(ws),
+                           ws_bytes, _s(stream))
+
+
+def boba_nbr_workspace_bytes(n_rows, nnz):
+    return load().boba_nbr_workspace_bytes(n_rows, nnz)
+
+
+def boba_tune_get(kernel, size):
+    return load().boba_tune_get(kernel, size)
+
+
+def boba_tune_set(kernel, size, variant):
+    load().boba_tune_set(kernel, size, variant)
+
+
+def boba_tune_save(path):
+    return load().boba_tune_save(str(path).encode())
+
+
+def boba_tune_load(path):
+    return load().boba_tune_load(str(path).encode())
+
+
+def boba_tune_reset():
+    load().boba_tune_reset()
+
+
+def boba_timing_enable(on):
+    load().boba_timing_enable(int(on))
+
+
+def boba_version():
+    return load().boba_version().decode()
+
+
 def boba_stream_status(stream=None):
     return load().boba_stream_status(_s(stream))
 

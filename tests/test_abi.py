@@ -76,3 +76,23 @@ def test_no_oracle_in_product():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "boba_oracle" not in text and "liboracle" not in text, f
+
+
+def test_python_binding_has_every_entry_point():
+    """Every C entry point has a same-name Python function (the tuning/timing/server
+    families through their helpers or the serve module)."""
+    import paper_2306_10410_gb300 as pkg
+    from paper_2306_10410_gb300 import serve
+    missing = []
+    for name in declared_symbols():
+        if hasattr(pkg, name):
+            continue
+        method = {"create": "__init__", "destroy": "close"}.get(name[len("boba_server_"):],
+                                                               name[len("boba_server_"):])
+        if name.startswith("boba_server_") and hasattr(serve.Server, method):
+            continue
+        if name.startswith(("boba_timing_", "boba_tune_reorder", "boba_tune_batched",
+                            "boba_tune_spmv")):
+            continue                 # wrapped by kernel_timing() and tune_*()
+        missing.append(name)
+    assert not missing, missing
