@@ -138,6 +138,22 @@ boba_status_t boba_reorder_static(const int32_t *src, const int32_t *dst, int64_
                                   int32_t *perm_out, int32_t *src_out, int32_t *dst_out,
                                   uint32_t *error_bits, void *stream);
 
+/*
+ * boba_reorder_variant -- boba_reorder_ex with another reading of the method:
+ *   variant 0  first occurrence in I ++ J (the default; same as boba_reorder_ex)
+ *   variant 1  first occurrence in the interleaved list I(0) J(0) I(1) J(1) ...,
+ *              the flattening drawn in Fig. 1 (deterministic, bit-exact)
+ *   variant 2  Alg. 2 exactly as printed (Sec. 4.5): a plain, racy store instead
+ *              of AtomicMin, which the paper found as good in practice.  The
+ *              chosen key of a vertex is one of its positions but not always the
+ *              lowest, so the result may differ from run to run; it is always a
+ *              valid permutation with consistent edges.
+ * ws: boba_reorder_workspace_bytes(m, n) bytes.
+ */
+boba_status_t boba_reorder_variant(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                                   int32_t *perm_out, int32_t *src_out, int32_t *dst_out,
+                                   int variant, void *ws, size_t ws_bytes, void *stream);
+
 /* ------------------------------------------------------------------------
  * The reorder's phases as separate calls (sharding one graph over devices)
  * ------------------------------------------------------------------------ */

@@ -17,7 +17,7 @@ __all__ = [
     "boba_reorder", "boba_reorder_ex", "boba_reorder_workspace_bytes", "boba_reorder_static", "boba_reorder_batched",
     "boba_reorder_batched_workspace_bytes", "boba_batched_set_mode", "boba_coo_to_csr", "boba_coo_to_csr_workspace_bytes",
     "boba_spmv_csr", "boba_spmv_workspace_bytes", "boba_stream_status", "boba_status_string",
-    "Workspace", "kernel_timing", "nbr", "sort_by_dst", "tune_reorder", "tune_batched", "tune_spmv", "tune_save",
+    "Workspace", "kernel_timing", "nbr", "reorder_variant", "sort_by_dst", "tune_reorder", "tune_batched", "tune_spmv", "tune_save",
     "tune_load", "tune_reset", "TUNE_FIRST", "TUNE_RELABEL", "TUNE_BATCHED", "TUNE_SPMV",
 ]
 
@@ -102,6 +102,24 @@ def boba_spmv_csr(row_ptr, col, val, x, y, n_rows, nnz, ws, ws_bytes, stream=Non
 
 def boba_spmv_workspace_bytes(n_rows, nnz):
     return load().boba_spmv_workspace_bytes(n_rows, nnz)
+
+
+def boba_reorder_variant(src, dst, m, n, perm_out, src_out, dst_out, variant, ws, ws_bytes,
+                         stream=None):
+    return load().boba_reorder_variant(_p(src), _p(dst), m, n, _p(perm_out), _p(src_out),
+                                       _p(dst_out), int(variant), _p(ws), ws_bytes, _s(stream))
+
+
+def reorder_variant(src, dst, n, variant, *, ws=None, stream=None):
+    """(perm, src_out, dst_out) for a reading of the method: 0 I ++ J, 1 interleaved
+    (Fig. 1), 2 racy store (Alg. 2 as printed)."""
+    m = src.numel()
+    perm = torch.empty(n, dtype=torch.int32, device=src.device)
+    so, do = torch.empty_like(src), torch.empty_like(dst)
+    buf = _ws(ws, boba_reorder_workspace_bytes(m, n), src.device)
+    check(boba_reorder_variant(src, dst, m, n, perm, so, do, variant, buf, buf.numel(), stream),
+          "boba_reorder_variant")
+    return perm, so, do
 
 
 def boba_first_keys(src, dst, m_local, pos_src, pos_dst, n, key, init, stream=None):

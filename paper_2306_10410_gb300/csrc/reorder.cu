@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(256) k_init(uint32_t *__restrict__ key, int64_
 // read most earlier positions are already recorded and the filtering read
 // (key[v] <= i) skips the atomic.
 // ---------------------------------------------------------------------------
-template <bool VEC, int BLOCK, int U>
+template <bool VEC, int BLOCK, int U, bool ATOMIC = true>
 __device__ __forceinline__ void first_body(const int32_t *__restrict__ src,
                                                        const int32_t *__restrict__ dst, int64_t m,
                                                        uint32_t n, uint32_t *key, uint32_t *status,
@@ -93,7 +93,7 @@ __device__ __forceinline__ void first_body(const int32_t *__restrict__ src,
                 for (int j = 0; j < 4; ++j) {
                     const int32_t v = comp(q[u], j);
                     if ((uint32_t)v >= n) raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE);
-                    else first_update(v, p0[u] + (uint32_t)j, cur[u][j], key);
+                    else first_update<ATOMIC>(v, p0[u] + (uint32_t)j, cur[u][j], key);
                 }
             }
         }
@@ -107,7 +107,7 @@ __device__ __forceinline__ void first_body(const int32_t *__restrict__ src,
         const int32_t v = ld_stream((hi ? dst : src) + e);
         const uint32_t pos = (uint32_t)((hi ? pos_dst : pos_src) + e);
         if ((uint32_t)v >= n) raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE);
-        else first_update(v, pos, key[v], key);
+        else first_update<ATOMIC>(v, pos, key[v], key);
     }
 }
 
@@ -128,6 +128,49 @@ __global__ void __launch_bounds__(kFirstBlock) k_first_at(const int32_t *__restr
                                                           int64_t pos_src, int64_t pos_dst)
 {
     first_body<VEC, kFirstBlock, kFirstUnroll>(src, dst, m, n, key, status, pos_src, pos_dst);
+}
+
+// Alg. 2 exactly as printed (Sec. 4.5): the same sweep with a plain store in
+// place of the AtomicMin.  Faster under contention, not deterministic.
+template <bool VEC>
+__global__ void __launch_bounds__(kFirstBlock) k_first_racy(const int32_t *__restrict__ src,
+                                                            const int32_t *__restrict__ dst, int64_t m,
+                                                            uint32_t n, uint32_t *key, uint32_t *status)
+{
+    first_body<VEC, kFirstBlock, kFirstUnroll, false>(src, dst, m, n, key, status, 0, m);
+}
+
+// The interleaved flattening drawn in Fig. 1: I(0) J(0) I(1) J(1) ..., edge e's
+// source at position 2e and its destination at 2e + 1.
+__global__ void __launch_bounds__(256) k_first_interleaved(const int32_t *__restrict__ src,
+                                                           const int32_t *__restrict__ dst,
+                                                           int64_t m, uint32_t n, uint32_t *key,
+                                                           uint32_t *status)
+{
+    constexpr int U = 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * U;
+    for (int64_t b = ((int64_t)blockIdx.x * blockDim.x) * U + threadIdx.x; b < m; b += stride) {
+        int32_t vs[U], vd[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t e = b + (int64_t)u * blockDim.x;
+            vs[u] = vd[u] = -1;
+            if (e < m) {
+                vs[u] = ld_stream(src + e);
+                vd[u] = ld_stream(dst + e);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t e = b + (int64_t)u * blockDim.x;
+            if (e >= m) continue;
+            const uint32_t p = (uint32_t)(2 * e);
+            if ((uint32_t)vs[u] < n) first_update(vs[u], p, key[vs[u]], key);
+            else raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE);
+            if ((uint32_t)vd[u] < n) first_update(vd[u], p + 1, key[vd[u]], key);
+            else raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE);
+        }
+    }
 }
 
 // Variants for the autotuner (vector path): BLOCK threads, U int4 loads in flight.
@@ -396,7 +439,25 @@ boba_status_t launch_reorder(const ReorderArgs &a, int64_t n4, size_t nzero_u32,
         BOBA_TIMED("reorder.init", stream,
                    k_init<<<g, 256, 0, stream>>>(a.key, n4, a.bitmap, (int64_t)nzero_u32));
     }
-    if (a.m > 0) {
+    if (a.m > 0 && a.variant != 0) {
+        const bool vec = aligned16(a.src) && aligned16(a.dst);
+        const int64_t work = cdiv(2 * a.m, 4 * kFirstBlock * kFirstUnroll);
+        if (a.variant == 1) {
+            const int g = persistent_grid((const void *)k_first_interleaved, 256, cdiv(a.m, 1024));
+            BOBA_TIMED("reorder.first", stream,
+                       k_first_interleaved<<<g, 256, 0, stream>>>(a.src, a.dst, a.m, a.n, a.key, a.status));
+        } else if (vec) {
+            const int g = persistent_grid((const void *)k_first_racy<true>, kFirstBlock, work);
+            BOBA_TIMED("reorder.first", stream,
+                       k_first_racy<true><<<g, kFirstBlock, 0, stream>>>(a.src, a.dst, a.m, a.n, a.key,
+                                                                        a.status));
+        } else {
+            const int g = persistent_grid((const void *)k_first_racy<false>, kFirstBlock, work * 4);
+            BOBA_TIMED("reorder.first", stream,
+                       k_first_racy<false><<<g, kFirstBlock, 0, stream>>>(a.src, a.dst, a.m, a.n,
+                                                                         a.key, a.status));
+        }
+    } else if (a.m > 0) {
         const bool vec = aligned16(a.src) && aligned16(a.dst);
         const int64_t work = cdiv(2 * a.m, 4 * kFirstBlock * kFirstUnroll);
         if (vec && launch_first_variant(tuned_variant(kTuneFirst, a.m), a, stream)) {
@@ -412,6 +473,8 @@ boba_status_t launch_reorder(const ReorderArgs &a, int64_t n4, size_t nzero_u32,
                        k_first<false><<<g, kFirstBlock, 0, stream>>>(a.src, a.dst, a.m, a.n, a.key,
                                                                     a.status));
         }
+    }
+    if (a.m > 0) {
         const int gm = persistent_grid((const void *)k_mark, 256, cdiv(n4 / 4, 256));
         BOBA_TIMED("reorder.mark", stream, k_mark<<<gm, 256, 0, stream>>>(a.key, n4, a.bitmap));
         BOBA_TIMED("reorder.scan", stream,
@@ -631,4 +694,47 @@ extern "C" boba_status_t boba_relabel(const int32_t *src, const int32_t *dst, in
     }
     BOBA_LAUNCH_CHECK();
     return BOBA_OK;
+}
+
+extern "C" boba_status_t boba_reorder_variant(const int32_t *src, const int32_t *dst, int64_t m,
+                                              int64_t n, int32_t *perm_out, int32_t *src_out,
+                                              int32_t *dst_out, int variant, void *ws,
+                                              size_t ws_bytes, void *stream_)
+{
+    if (variant < 0 || variant > 2) return BOBA_ERR_INVALID_ARG;
+    if (m < 0 || n < 0) return BOBA_ERR_INVALID_ARG;
+    if (m > kMaxSize || n > kMaxSize) return BOBA_ERR_TOO_LARGE;
+    if (n == 0 && m > 0) return BOBA_ERR_INVALID_ARG;
+    if ((src_out == nullptr) != (dst_out == nullptr)) return BOBA_ERR_INVALID_ARG;
+    if (n == 0) return BOBA_OK;
+    if (perm_out == nullptr || ws == nullptr) return BOBA_ERR_INVALID_ARG;
+    if (m > 0 && (src == nullptr || dst == nullptr)) return BOBA_ERR_INVALID_ARG;
+    ReorderLayout L;
+    reorder_layout(m, n, L);
+    if (ws_bytes < L.total || !aligned256(ws)) return BOBA_ERR_WORKSPACE;
+    const DeviceInfo *dev = device_info();
+    if (!dev) return BOBA_ERR_CUDA;
+    char *base = static_cast<char *>(ws);
+    ReorderArgs a;
+    a.src = src;
+    a.dst = dst;
+    a.m = m;
+    a.n = (uint32_t)n;
+    a.key = reinterpret_cast<uint32_t *>(base + L.key);
+    a.label = reinterpret_cast<int32_t *>(base + L.label);
+    a.perm = perm_out;
+    a.bitmap = reinterpret_cast<uint32_t *>(base + L.bitmap);
+    a.grp = reinterpret_cast<uint32_t *>(base + L.grp);
+    a.tstat_scan = reinterpret_cast<uint64_t *>(base + L.tstat_scan);
+    a.tstat_emit = reinterpret_cast<uint64_t *>(base + L.tstat_emit);
+    a.counters = reinterpret_cast<uint32_t *>(base + L.counters);
+    a.nwords = L.nwords;
+    a.scan_tiles = L.scan_tiles;
+    a.emit_tiles = L.emit_tiles;
+    a.status = dev->status;
+    a.src_out = src_out;
+    a.dst_out = dst_out;
+    a.label_vec = true;
+    a.variant = variant;
+    return launch_reorder(a, L.n4, (L.zero_end - L.zero_begin) / 4, static_cast<cudaStream_t>(stream_));
 }

@@ -33,15 +33,23 @@ struct ReorderArgs {
     uint32_t *status;
     int32_t *src_out, *dst_out;
     bool label_vec;
+    int variant = 0;          // 0 first occurrence in I ++ J, 1 interleaved, 2 racy store
 };
 
 // One position of I ++ J: lower key[v] to `pos` unless a position already
 // recorded for v is lower.  The filtering read may see a stale value: keys only
 // ever decrease, so a stale key is >= the current one and at worst costs an
 // atomic that changes nothing; the minimum itself is taken by atomicMin.
+template <bool ATOMIC = true>
 __device__ __forceinline__ void first_update(int32_t v, uint32_t pos, uint32_t cur, uint32_t *key)
 {
-    if (cur > pos) atomicMin(&key[v], pos);
+    if constexpr (ATOMIC) {
+        if (cur > pos) atomicMin(&key[v], pos);
+    } else {
+        // Alg. 2 exactly as printed: a plain, racy store (the result depends
+        // on timing; the minimum is not guaranteed)
+        if (cur > pos) key[v] = pos;
+    }
 }
 
 // Rank of a finite key among all first-occurrence positions: the popcount of

@@ -1,0 +1,71 @@
+"""Other readings of the method: the interleaved flattening of Fig. 1 (bit-exact
+against the oracle, which reproduces the figure) and Alg. 2 as printed with its
+racy store (valid, not unique)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def boba():
+    import paper_2306_10410_gb300 as b
+    b.load()
+    return b
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).cuda()
+
+
+def test_fig1_interleaved_on_gpu(boba, golden):
+    g = golden("fig1_star.txt")
+    alphabet = sorted(set(g["I"]) | set(g["J"]))
+    I = [alphabet.index(t) for t in g["I"]]
+    J = [alphabet.index(t) for t in g["J"]]
+    perm, _, _ = boba.reorder_variant(dev(I), dev(J), len(alphabet), 1)
+    boba.stream_status()
+    assert [alphabet[v] for v in perm.cpu().numpy()] == g["uniquified"]
+
+
+@pytest.mark.parametrize("m", [1, 5, 1001, 262144])
+def test_interleaved_matches_oracle(boba, m):
+    n = max(2, m // 8)
+    I, J = synth.rmat(max(1, int(np.ceil(np.log2(n)))), m, seed=m, n=n)
+    perm, so, do = boba.reorder_variant(dev(I), dev(J), n, 1)
+    boba.stream_status()
+    operm, olab = oracle.boba_perm_interleaved(I, J, n)
+    oso, odo = oracle.relabel(I, J, olab, n)
+    np.testing.assert_array_equal(perm.cpu().numpy(), operm)
+    np.testing.assert_array_equal(so.cpu().numpy(), oso)
+    np.testing.assert_array_equal(do.cpu().numpy(), odo)
+
+
+def test_variant0_is_the_default(boba):
+    I, J = synth.RMAT14.generate()
+    n = synth.RMAT14.n
+    p0, s0, d0 = boba.reorder_variant(dev(I), dev(J), n, 0)
+    p1, s1, d1 = boba.reorder(dev(I), dev(J), n)
+    boba.stream_status()
+    assert torch.equal(p0, p1) and torch.equal(s0, s1) and torch.equal(d0, d1)
+
+
+def test_racy_store_is_valid_and_close(boba):
+    I, J = synth.rmat(18, 1 << 22, seed=14)
+    n = 1 << 18
+    perm, so, do = boba.reorder_variant(dev(I), dev(J), n, 2)
+    boba.stream_status()
+    p, s, d = perm.cpu().numpy(), so.cpu().numpy(), do.cpu().numpy()
+    assert np.array_equal(np.sort(p), np.arange(n))                 # a permutation
+    assert np.array_equal(p[s], I) and np.array_equal(p[d], J)      # edges consistent
+    app = len(np.unique(np.concatenate([I, J])))
+    assert np.all(np.diff(p[app:]) > 0)                             # isolated tail ascending
+    # quality: NBR of the racy ordering close to the exact one (Sec. 4.5's claim)
+    operm, oso, odo = oracle.reorder(I, J, n)
+    v_exact, _ = boba.nbr(*[torch.from_numpy(a).cuda() for a in oracle.coo_to_csr(oso, odo, n)[:2]])
+    v_racy, _ = boba.nbr(*[torch.from_numpy(a).cuda() for a in oracle.coo_to_csr(s, d, n)[:2]])
+    assert abs(v_racy - v_exact) < 0.05
