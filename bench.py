@@ -226,7 +226,8 @@ def run_ours(args):
     tuning = None
     if args.tune_spec:
         # fixed variants (reproducible profiling): "first=5,relabel=3,spmv=5"
-        fam = {"first": boba.TUNE_FIRST, "relabel": boba.TUNE_RELABEL, "spmv": boba.TUNE_SPMV}
+        fam = {"first": boba.TUNE_FIRST, "relabel": boba.TUNE_RELABEL, "spmv": boba.TUNE_SPMV,
+               "csr": boba.TUNE_CSR}
         tuning = {}
         for item in args.tune_spec.split(","):
             k, v = item.split("=")
@@ -238,6 +239,7 @@ def run_ours(args):
         tuning = boba.tune_reorder(src, dst, n, reps=3)
         if have_csr:
             reorder()
+            tuning.update(boba.tune_csr(so, do, n, reps=2))
             csr()
             tuning.update(boba.tune_spmv(row_ptr, col, val, x, reps=3))
         boba.stream_status(stream)

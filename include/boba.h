@@ -404,7 +404,8 @@ const char *boba_version(void);
  * ------------------------------------------------------------------------ */
 
 /* Kernel families with tuned variants (the `kernel` argument below). */
-enum { BOBA_TUNE_FIRST = 0, BOBA_TUNE_RELABEL = 1, BOBA_TUNE_BATCHED = 2, BOBA_TUNE_SPMV = 3 };
+enum { BOBA_TUNE_FIRST = 0, BOBA_TUNE_RELABEL = 1, BOBA_TUNE_BATCHED = 2, BOBA_TUNE_SPMV = 3,
+       BOBA_TUNE_CSR = 4 };
 
 /*
  * boba_tune_reorder -- times every variant (block size x loads in flight) of
@@ -441,6 +442,15 @@ boba_status_t boba_tune_batched(const int32_t *src, const int32_t *dst, const in
 boba_status_t boba_tune_spmv(const int64_t *row_ptr, const int32_t *col, const float *val,
                              const float *x, float *y, int64_t n_rows, int64_t nnz, void *ws,
                              size_t ws_bytes, int reps, int *chosen, void *stream);
+
+/*
+ * boba_tune_csr -- the same for the in-tile ranking of boba_coo_to_csr's radix
+ * passes (variant 0: warp match instruction; 1: eight bit ballots), keyed by
+ * m; every variant's CSR must equal the default's bit for bit.
+ */
+boba_status_t boba_tune_csr(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                            int64_t *row_ptr, int32_t *col_out, float *val_out, void *ws,
+                            size_t ws_bytes, int reps, int *chosen, void *stream);
 
 /* The tuned variant for a kernel family and size (0 = default), and setting it
  * by hand (variant -1 clears it). */

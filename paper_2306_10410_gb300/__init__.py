@@ -18,10 +18,11 @@ __all__ = [
     "boba_reorder_batched_workspace_bytes", "boba_batched_set_mode", "boba_coo_to_csr", "boba_coo_to_csr_workspace_bytes",
     "boba_spmv_csr", "boba_spmv_workspace_bytes", "boba_stream_status", "boba_status_string",
     "Workspace", "kernel_timing", "nbr", "reorder_variant", "sort_by_dst", "tune_reorder", "tune_batched", "tune_spmv", "tune_save",
-    "tune_load", "tune_reset", "TUNE_FIRST", "TUNE_RELABEL", "TUNE_BATCHED", "TUNE_SPMV",
+    "tune_load", "tune_reset", "tune_csr", "TUNE_FIRST", "TUNE_RELABEL", "TUNE_BATCHED",
+    "TUNE_SPMV", "TUNE_CSR",
 ]
 
-TUNE_FIRST, TUNE_RELABEL, TUNE_BATCHED, TUNE_SPMV = 0, 1, 2, 3
+TUNE_FIRST, TUNE_RELABEL, TUNE_BATCHED, TUNE_SPMV, TUNE_CSR = 0, 1, 2, 3, 4
 
 
 def _p(t):
@@ -392,6 +393,18 @@ def tune_spmv(row_ptr, col, val, x, *, reps=3, stream=None):
     check(load().boba_tune_spmv(_p(row_ptr), _p(col), _p(val), _p(x), _p(y), n_rows, nnz, _p(buf),
                                 buf.numel(), reps, ch, _s(stream)), "boba_tune_spmv")
     return {"spmv": ch[0]}
+
+
+def tune_csr(src, dst, n, *, reps=3, stream=None):
+    m = src.numel()
+    row_ptr = torch.empty(n + 1, dtype=torch.int64, device=src.device)
+    col = torch.empty(m, dtype=torch.int32, device=src.device)
+    val = torch.empty(m, dtype=torch.float32, device=src.device)
+    buf = _ws(None, boba_coo_to_csr_workspace_bytes(m, n), src.device)
+    ch = _i2()
+    check(load().boba_tune_csr(_p(src), _p(dst), m, n, _p(row_ptr), _p(col), _p(val), _p(buf),
+                               buf.numel(), reps, ch, _s(stream)), "boba_tune_csr")
+    return {"csr": ch[0]}
 
 
 def tune_save(path):

@@ -64,6 +64,7 @@ SIGNATURES = {
     "boba_tune_batched": (_ST, [_P, _P, _P, _P, _I64, _I64, _I64, _I64, _I64, _P, _P, _P, _P,
                                 _SZ, ctypes.c_int, _P, _P]),
     "boba_tune_spmv": (_ST, [_P, _P, _P, _P, _P, _I64, _I64, _P, _SZ, ctypes.c_int, _P, _P]),
+    "boba_tune_csr": (_ST, [_P, _P, _I64, _I64, _P, _P, _P, _P, _SZ, ctypes.c_int, _P, _P]),
     "boba_tune_get": (ctypes.c_int, [ctypes.c_int, _I64]),
     "boba_tune_set": (None, [ctypes.c_int, _I64, ctypes.c_int]),
     "boba_tune_save": (_ST, [ctypes.c_char_p]),

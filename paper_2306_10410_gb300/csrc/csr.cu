@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256) k_csr_digits(const uint32_t *__restrict__
 // One stable LSD pass over digit p (bits 8p .. 8p+7).  BLOCK threads hold
 // ITEMS items each; the first 256 threads also own one digit each for the
 // cross-tile look-back.
-template <int BLOCK, int ITEMS>
+template <int BLOCK, int ITEMS, bool BALLOT = false>
 __global__ void __launch_bounds__(BLOCK) k_csr_pass(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t m, int p, const uint32_t *__restrict__ dstart,
@@ -167,7 +167,20 @@ __global__ void __launch_bounds__(BLOCK) k_csr_pass(
         const int64_t i = t0 + warp * WARP_ITEMS + k * 32 + lane;
         const bool valid = i < m;
         const uint32_t d = valid ? ((key[k] >> shift) & 255u) : 256u;
-        const unsigned peers = __match_any_sync(kFull, d);
+        unsigned peers;
+        if constexpr (BALLOT) {
+            // lanes with the same digit: intersect 8 bit-ballots (and the
+            // valid/invalid split) instead of one match instruction
+            const unsigned vm = __ballot_sync(kFull, valid);
+            peers = valid ? vm : ~vm;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const unsigned bm = __ballot_sync(kFull, (d >> b) & 1u);
+                peers &= ((d >> b) & 1u) ? bm : ~bm;
+            }
+        } else {
+            peers = __match_any_sync(kFull, d);
+        }
         const int leader = __ffs(peers) - 1;
         uint32_t old = 0;
         if (valid && lane == leader) {
@@ -710,9 +723,15 @@ extern "C" boba_status_t boba_coo_to_csr(const int32_t *src, const int32_t *dst,
         const bool last = p == L.passes - 1;
         uint32_t *ko = (p & 1) ? kB : kA;
         uint32_t *vo = last ? reinterpret_cast<uint32_t *>(col_out) : ((p & 1) ? vB : vA);
-        BOBA_TIMED("csr.pass", stream,
-                   k_csr_pass<kPassBlock, kPassItems><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
-                       kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status, p, 0));
+        if (tuned_variant(kTuneCsr, m) == 1)
+            BOBA_TIMED("csr.pass", stream,
+                       k_csr_pass<kPassBlock, kPassItems, true><<<(unsigned)L.tiles, kPassBlock, 0,
+                                                                 stream>>>(
+                           kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status, p, 0));
+        else
+            BOBA_TIMED("csr.pass", stream,
+                       k_csr_pass<kPassBlock, kPassItems><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
+                           kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status, p, 0));
         kin = ko;
         vin = vo;
     }

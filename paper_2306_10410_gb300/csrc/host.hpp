@@ -49,7 +49,7 @@ void timing_end(int slot, cudaStream_t s);
 // Autotuned choices: the variant index picked for a kernel family and a size
 // (bucketed by log2 of the size), or 0 (the default variant) if none.
 enum TuneKernel { kTuneFirst = 0, kTuneRelabel = 1, kTuneBatched = 2, kTuneSpmv = 3,
-                  kTuneKernels = 4 };
+                  kTuneCsr = 4, kTuneKernels = 5 };
 int tuned_variant(int kernel, int64_t size);
 int size_class(int64_t size);
 

@@ -22,8 +22,8 @@ namespace {
 
 constexpr int kClasses = 64;
 constexpr int kMaxDev = 64;
-constexpr int kVariants[kTuneKernels] = {6, 6, 2, 6};   // first, relabel, batched, spmv
-const char *kNames[kTuneKernels] = {"first", "relabel", "batched", "spmv"};
+constexpr int kVariants[kTuneKernels] = {6, 6, 2, 6, 2};   // first, relabel, batched, spmv, csr
+const char *kNames[kTuneKernels] = {"first", "relabel", "batched", "spmv", "csr"};
 
 std::mutex g_tmu;
 signed char g_table[kMaxDev][kTuneKernels][kClasses];
@@ -280,6 +280,53 @@ extern "C" boba_status_t boba_tune_spmv(const int64_t *row_ptr, const int32_t *c
     }
     set_entry(kTuneSpmv, cls, best);
     if (chosen) chosen[0] = best;
+    if (cudaGetLastError() != cudaSuccess) return BOBA_ERR_CUDA;
+    return st;
+}
+
+extern "C" boba_status_t boba_tune_csr(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                                       int64_t *row_ptr, int32_t *col_out, float *val_out, void *ws,
+                                       size_t ws_bytes, int reps, int *chosen, void *stream_)
+{
+    if (reps < 1 || m <= 0 || n <= 0) return BOBA_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream_);
+    const int cls = size_class(m);
+    void *ref = nullptr;
+    unsigned long long *dcnt = nullptr;
+    if (cudaMalloc(&ref, (size_t)m * 8 + (size_t)(n + 1) * 8) != cudaSuccess ||
+        cudaMalloc(&dcnt, 8) != cudaSuccess) {
+        (void)cudaGetLastError();
+        if (ref) cudaFree(ref);
+        return BOBA_ERR_CUDA;
+    }
+    int32_t *rcol = static_cast<int32_t *>(ref);
+    float *rval = reinterpret_cast<float *>(rcol + m);
+    int64_t *rrp = reinterpret_cast<int64_t *>(rval + m);
+    auto run = [&] {
+        return boba_coo_to_csr(src, dst, m, n, row_ptr, col_out, val_out, ws, ws_bytes, s);
+    };
+    boba_status_t st = BOBA_OK;
+    int best = 0;
+    double best_ms = 1e30;
+    for (int v = 0; v < kVariants[kTuneCsr]; ++v) {
+        set_entry(kTuneCsr, cls, v);
+        if ((st = run()) != BOBA_OK) break;
+        if (v == 0) {
+            cudaMemcpyAsync(rcol, col_out, 4 * (size_t)m, cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(rval, val_out, 4 * (size_t)m, cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(rrp, row_ptr, 8 * (size_t)(n + 1), cudaMemcpyDeviceToDevice, s);
+        } else if (count_diff(col_out, rcol, m, dcnt, s) != 0 ||
+                   count_diff(val_out, rval, m, dcnt, s) != 0 ||
+                   count_diff(row_ptr, rrp, 2 * (n + 1), dcnt, s) != 0) {
+            continue;
+        }
+        const double t = time_ms(run, reps, s);
+        if (t < best_ms) { best_ms = t; best = v; }
+    }
+    set_entry(kTuneCsr, cls, best);
+    if (chosen) chosen[0] = best;
+    cudaFree(ref);
+    cudaFree(dcnt);
     if (cudaGetLastError() != cudaSuccess) return BOBA_ERR_CUDA;
     return st;
 }

@@ -92,7 +92,7 @@ def test_python_binding_has_every_entry_point():
         if name.startswith("boba_server_") and hasattr(serve.Server, method):
             continue
         if name.startswith(("boba_timing_", "boba_tune_reorder", "boba_tune_batched",
-                            "boba_tune_spmv")):
+                            "boba_tune_spmv", "boba_tune_csr")):
             continue                 # wrapped by kernel_timing() and tune_*()
         missing.append(name)
     assert not missing, missing

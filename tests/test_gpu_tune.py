@@ -85,3 +85,19 @@ def test_tune_batched_and_spmv(boba):
         err = np.linalg.norm(y.cpu().numpy() - y64) / np.linalg.norm(y64)
         assert err <= 1e-5, (v, err)
     boba.tune_reset()
+
+
+def test_csr_ranking_variants_bit_identical(boba):
+    I, J = synth.rmat(17, 800_001, seed=35)
+    n = 1 << 17
+    orp, ocol, oval = oracle.coo_to_csr(I, J, n)
+    for v in (0, 1):
+        boba.load().boba_tune_set(boba.TUNE_CSR, len(I), v)
+        rp, col, val = boba.coo_to_csr(torch.from_numpy(I).cuda(), torch.from_numpy(J).cuda(), n)
+        boba.stream_status()
+        np.testing.assert_array_equal(rp.cpu().numpy(), orp)
+        np.testing.assert_array_equal(col.cpu().numpy(), ocol)
+        np.testing.assert_array_equal(val.cpu().numpy(), oval)
+    ch = boba.tune_csr(torch.from_numpy(I).cuda(), torch.from_numpy(J).cuda(), n, reps=2)
+    assert ch["csr"] in (0, 1)
+    boba.tune_reset()
