@@ -434,8 +434,9 @@ boba_status_t boba_tune_batched(const int32_t *src, const int32_t *dst, const in
 
 /*
  * boba_tune_spmv -- the same for boba_spmv_csr (variant 0: lanes per row
- * chosen from nnz / n_rows; 1..4: 4, 8, 16, 32 lanes per row; 5: merge-path
- * decomposition over row ends and nonzeros), keyed by nnz.  The variants sum
+ * chosen from nnz / n_rows; 1..4: 4, 8, 16, 32 lanes per row; 5..8: merge-path
+ * decomposition over row ends and nonzeros with 256x8, 256x12, 512x8, 128x16
+ * threads x items per tile), keyed by nnz.  The variants sum
  * in different orders, so their results may differ in the last bits; each is
  * deterministic.
  */

@@ -193,11 +193,12 @@ __device__ __forceinline__ void mp_search(const int64_t *__restrict__ row_ptr, i
 }
 
 __global__ void __launch_bounds__(256) k_mp_partition(const int64_t *__restrict__ row_ptr, int64_t n,
-                                                      int64_t nnz, int64_t tiles, int2 *part)
+                                                      int64_t nnz, int64_t tiles, int64_t tile_items,
+                                                      int2 *part)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t > tiles) return;
-    const int64_t d = t * kMpTile < n + nnz ? t * kMpTile : n + nnz;
+    const int64_t d = t * tile_items < n + nnz ? t * tile_items : n + nnz;
     int64_t x, y;
     mp_search(row_ptr, n, nnz, d, x, y);
     part[t] = make_int2((int)x, (int)y);
@@ -208,12 +209,14 @@ struct KV {
     float v;
 };
 
-__global__ void __launch_bounds__(kMpBlock) k_mp_spmv(
+template <int MB, int MI>
+__global__ void __launch_bounds__(MB) k_mp_spmv(
     const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
     const float *__restrict__ val, const float *__restrict__ x, float *__restrict__ y, int64_t n,
     int64_t nnz, const int2 *__restrict__ part, int32_t *__restrict__ carry_row,
     float *__restrict__ carry_val)
 {
+    constexpr int kMpBlock = MB, kMpItems = MI, kMpTile = MB * MI;
     __shared__ int32_t s_end[kMpTile + 1];     // row ends of the tile's rows, relative to y0
     __shared__ float s_prod[kMpTile];          // products of the tile's nonzeros
     __shared__ KV s_warp[kMpBlock / 32];
@@ -363,20 +366,32 @@ extern "C" boba_status_t boba_spmv_csr(const int64_t *row_ptr, const int32_t *co
     float *partial = reinterpret_cast<float *>(b + L.partial);
     const uint32_t cap = (uint32_t)L.cap;
 
-    const int tv = tuned_variant(kTuneSpmv, nnz);   // 0 auto, 1..4: LPR 4, 8, 16, 32, 5 merge path
-    if (tv == 5) {
+    const int tv = tuned_variant(kTuneSpmv, nnz);
+    // 0 auto, 1..4: LPR 4, 8, 16, 32; 5..8: merge path (block x items) 256x8, 256x12, 512x8, 128x16
+    if (tv >= 5 && tv <= 8) {
         int2 *part = reinterpret_cast<int2 *>(b + L.mp_part);
         int32_t *crow = reinterpret_cast<int32_t *>(b + L.mp_crow);
         float *cval = reinterpret_cast<float *>(b + L.mp_cval);
+        const int items = tv == 5 ? 2048 : tv == 6 ? 3072 : tv == 7 ? 4096 : 2048;
+        const int64_t tiles = cdiv(n_rows + nnz, items);
         BOBA_TIMED("spmv.partition", stream,
-                   k_mp_partition<<<(unsigned)cdiv(L.mp_tiles + 1, 256), 256, 0, stream>>>(
-                       row_ptr, n_rows, nnz, L.mp_tiles, part));
-        BOBA_TIMED("spmv", stream,
-                   k_mp_spmv<<<(unsigned)L.mp_tiles, kMpBlock, 0, stream>>>(
-                       row_ptr, col, val, x, y, n_rows, nnz, part, crow, cval));
+                   k_mp_partition<<<(unsigned)cdiv(tiles + 1, 256), 256, 0, stream>>>(
+                       row_ptr, n_rows, nnz, tiles, items, part));
+        if (tv == 5)
+            BOBA_TIMED("spmv", stream, k_mp_spmv<256, 8><<<(unsigned)tiles, 256, 0, stream>>>(
+                                           row_ptr, col, val, x, y, n_rows, nnz, part, crow, cval));
+        else if (tv == 6)
+            BOBA_TIMED("spmv", stream, k_mp_spmv<256, 12><<<(unsigned)tiles, 256, 0, stream>>>(
+                                           row_ptr, col, val, x, y, n_rows, nnz, part, crow, cval));
+        else if (tv == 7)
+            BOBA_TIMED("spmv", stream, k_mp_spmv<512, 8><<<(unsigned)tiles, 512, 0, stream>>>(
+                                           row_ptr, col, val, x, y, n_rows, nnz, part, crow, cval));
+        else
+            BOBA_TIMED("spmv", stream, k_mp_spmv<128, 16><<<(unsigned)tiles, 128, 0, stream>>>(
+                                           row_ptr, col, val, x, y, n_rows, nnz, part, crow, cval));
         BOBA_TIMED("spmv.fixup", stream,
-                   k_mp_fixup<<<(unsigned)cdiv(L.mp_tiles, 256), 256, 0, stream>>>(
-                       crow, cval, L.mp_tiles, n_rows, y));
+                   k_mp_fixup<<<(unsigned)cdiv(tiles, 256), 256, 0, stream>>>(crow, cval, tiles,
+                                                                               n_rows, y));
         BOBA_LAUNCH_CHECK();
         return BOBA_OK;
     }
