@@ -217,20 +217,24 @@ __global__ void __launch_bounds__(MB) k_mp_spmv(
     float *__restrict__ carry_val)
 {
     constexpr int kMpBlock = MB, kMpItems = MI, kMpTile = MB * MI;
-    __shared__ int32_t s_end[kMpTile + 1];     // row ends of the tile's rows, relative to y0
-    __shared__ float s_prod[kMpTile];          // products of the tile's nonzeros
+    // one pad word per 32: a thread walks MI consecutive items, so without the
+    // padding the lanes of a warp would hit the same few banks
+    constexpr int kPadded = kMpTile + kMpTile / 32 + 2;
+    __shared__ int32_t s_end[kPadded];         // row ends of the tile's rows, relative to y0
+    __shared__ float s_prod[kPadded];          // products of the tile's nonzeros
     __shared__ KV s_warp[kMpBlock / 32];
+    auto P = [](int j) { return j + (j >> 5); };
     const int64_t tile = blockIdx.x;
     const int2 p0 = part[tile], p1 = part[tile + 1];
     const int x0 = p0.x, y0 = p0.y;
     const int nrows = p1.x - p0.x, nnzt = p1.y - p0.y;
     for (int i = threadIdx.x; i < nrows; i += kMpBlock)
-        s_end[i] = (int32_t)(__ldg(row_ptr + x0 + 1 + i) - y0);
-    if (threadIdx.x == 0) s_end[nrows] = 0x7FFFFFFF;      // sentinel: no row end beyond
+        s_end[P(i)] = (int32_t)(__ldg(row_ptr + x0 + 1 + i) - y0);
+    if (threadIdx.x == 0) s_end[P(nrows)] = 0x7FFFFFFF;   // sentinel: no row end beyond
 #pragma unroll
     for (int u = 0; u < kMpItems; ++u) {
         const int j = u * kMpBlock + threadIdx.x;
-        if (j < nnzt) s_prod[j] = __ldcs(val + y0 + j) * __ldg(x + __ldcs(col + y0 + j));
+        if (j < nnzt) s_prod[P(j)] = __ldcs(val + y0 + j) * __ldg(x + __ldcs(col + y0 + j));
     }
     __syncthreads();
     // this thread's split inside the tile
@@ -238,7 +242,7 @@ __global__ void __launch_bounds__(MB) k_mp_spmv(
     int lo = dt - nnzt > 0 ? dt - nnzt : 0, hi = dt < nrows ? dt : nrows;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (s_end[mid] <= dt - mid - 1) lo = mid + 1;
+        if (s_end[P(mid)] <= dt - mid - 1) lo = mid + 1;
         else hi = mid;
     }
     int xt = lo, yt = dt - lo;
@@ -250,8 +254,8 @@ __global__ void __launch_bounds__(MB) k_mp_spmv(
 #pragma unroll
     for (int i = 0; i < kMpItems; ++i) {
         if (xt + yt >= nrows + nnzt) break;
-        if (yt < s_end[xt]) {
-            acc += s_prod[yt];
+        if (yt < s_end[P(xt)]) {
+            acc += s_prod[P(yt)];
             ++yt;
         } else {
             if (first_end < 0) { first_end = xt; first_val = acc; }
