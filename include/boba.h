@@ -139,6 +139,25 @@ boba_status_t boba_reorder_static(const int32_t *src, const int32_t *dst, int64_
                                   uint32_t *error_bits, void *stream);
 
 /*
+ * boba_reorder_host -- boba_reorder for a graph in HOST memory: src, dst
+ * int32[m] in, perm int32[n] and src_out, dst_out int32[m] out, all HOST
+ * pointers (pinned memory makes the copies asynchronous and overlapped).  The
+ * edges move to the device in 2^24-edge chunks on an internal copy stream and
+ * each chunk's first-occurrence pass starts as soon as it has arrived; once
+ * the labels are known each chunk is relabelled and copied back on a second
+ * internal stream while the next one is relabelled.  Work on `stream` before
+ * the call happens before it, work after it sees the outputs.  The host
+ * buffers must stay valid until then.  Calls on one device enqueue one at a
+ * time (an internal lock).
+ *   ws  DEVICE scratch of boba_reorder_host_workspace_bytes(m, n) bytes
+ */
+boba_status_t boba_reorder_host(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
+                                int32_t *perm_out, int32_t *src_out, int32_t *dst_out, void *ws,
+                                size_t ws_bytes, void *stream);
+
+size_t boba_reorder_host_workspace_bytes(int64_t m, int64_t n);
+
+/*
  * boba_reorder_variant -- boba_reorder_ex with another reading of the method:
  *   variant 0  first occurrence in I ++ J (the default; same as boba_reorder_ex)
  *   variant 1  first occurrence in the interleaved list I(0) J(0) I(1) J(1) ...,

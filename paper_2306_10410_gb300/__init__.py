@@ -17,7 +17,7 @@ __all__ = [
     "boba_reorder", "boba_reorder_ex", "boba_reorder_workspace_bytes", "boba_reorder_static", "boba_reorder_batched",
     "boba_reorder_batched_workspace_bytes", "boba_batched_set_mode", "boba_coo_to_csr", "boba_coo_to_csr_workspace_bytes",
     "boba_spmv_csr", "boba_spmv_workspace_bytes", "boba_stream_status", "boba_status_string",
-    "Workspace", "kernel_timing", "nbr", "reorder_variant", "sort_by_dst", "tune_reorder", "tune_batched", "tune_spmv", "tune_save",
+    "Workspace", "kernel_timing", "nbr", "reorder_variant", "reorder_host", "sort_by_dst", "tune_reorder", "tune_batched", "tune_spmv", "tune_save",
     "tune_load", "tune_reset", "tune_csr", "TUNE_FIRST", "TUNE_RELABEL", "TUNE_BATCHED",
     "TUNE_SPMV", "TUNE_CSR",
 ]
@@ -103,6 +103,40 @@ def boba_spmv_csr(row_ptr, col, val, x, y, n_rows, nnz, ws, ws_bytes, stream=Non
 
 def boba_spmv_workspace_bytes(n_rows, nnz):
     return load().boba_spmv_workspace_bytes(n_rows, nnz)
+
+
+def _hp(t):
+    """Host tensor/array pointer (CPU tensors only)."""
+    if t is None:
+        return None
+    if hasattr(t, "is_cuda"):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("host buffers must be contiguous CPU tensors")
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+def boba_reorder_host(src, dst, m, n, perm_out, src_out, dst_out, ws, ws_bytes, stream=None):
+    return load().boba_reorder_host(_hp(src), _hp(dst), m, n, _hp(perm_out), _hp(src_out),
+                                    _hp(dst_out), _p(ws), ws_bytes, _s(stream))
+
+
+def boba_reorder_host_workspace_bytes(m, n):
+    return load().boba_reorder_host_workspace_bytes(m, n)
+
+
+def reorder_host(src, dst, n, *, perm_out=None, src_out=None, dst_out=None, ws=None, stream=None,
+                 device=None):
+    """BOBA of a graph in (preferably pinned) host memory; outputs in host memory."""
+    m = src.numel()
+    perm_out = torch.empty(n, dtype=torch.int32, pin_memory=True) if perm_out is None else perm_out
+    src_out = torch.empty(m, dtype=torch.int32, pin_memory=True) if src_out is None else src_out
+    dst_out = torch.empty(m, dtype=torch.int32, pin_memory=True) if dst_out is None else dst_out
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    buf = _ws(ws, boba_reorder_host_workspace_bytes(m, n), dev)
+    check(boba_reorder_host(src, dst, m, n, perm_out, src_out, dst_out, buf, buf.numel(), stream),
+          "boba_reorder_host")
+    return perm_out, src_out, dst_out
 
 
 def boba_reorder_variant(src, dst, m, n, perm_out, src_out, dst_out, variant, ws, ws_bytes,

@@ -33,6 +33,8 @@ SIGNATURES = {
     "boba_reorder": (_ST, [_P, _P, _I64, _I64, _P, _P, _P, _P]),
     "boba_reorder_workspace_bytes": (_SZ, [_I64, _I64]),
     "boba_reorder_ex": (_ST, [_P, _P, _I64, _I64, _P, _P, _P, _P, _P, _SZ, _P]),
+    "boba_reorder_host": (_ST, [_P, _P, _I64, _I64, _P, _P, _P, _P, _SZ, _P]),
+    "boba_reorder_host_workspace_bytes": (_SZ, [_I64, _I64]),
     "boba_reorder_variant": (_ST, [_P, _P, _I64, _I64, _P, _P, _P, ctypes.c_int, _P, _SZ, _P]),
     "boba_first_keys": (_ST, [_P, _P, _I64, _I64, _I64, _I64, _P, ctypes.c_int, _P]),
     "boba_labels_workspace_bytes": (_SZ, [_I64, _I64]),

@@ -423,6 +423,9 @@ template __global__ void k_first<true>(const int32_t *__restrict__, const int32_
                                        int64_t, uint32_t, uint32_t *, uint32_t *);
 template __global__ void k_first<false>(const int32_t *__restrict__, const int32_t *__restrict__,
                                         int64_t, uint32_t, uint32_t *, uint32_t *);
+template __global__ void k_first_at<true>(const int32_t *__restrict__, const int32_t *__restrict__,
+                                          int64_t, uint32_t, uint32_t *, uint32_t *, int64_t,
+                                          int64_t);
 template __global__ void k_relabel<true>(const int32_t *, const int32_t *, int64_t, uint32_t,
                                          const int32_t *__restrict__, int32_t *, int32_t *,
                                          uint32_t *);

@@ -229,3 +229,20 @@ def test_sharded_phases_equal_whole_graph(boba, shards):
     boba.stream_status()
     np.testing.assert_array_equal(p2.cpu().numpy(), operm)
     np.testing.assert_array_equal(s2.cpu().numpy(), oso)
+
+
+@pytest.mark.parametrize("m", [0, 1, 12345, (1 << 24) + 3, (1 << 25) + 17])
+def test_reorder_from_host_buffers(boba, m):
+    """boba_reorder_host (chunked copies overlapped with the kernels) equals the oracle,
+    also across chunk boundaries and with a ragged last chunk."""
+    n = max(1, min(1 << 20, m // 4 + 1))
+    I, J = synth.er(n, m, seed=m + 3) if m else (np.zeros(0, np.int32), np.zeros(0, np.int32))
+    src = torch.from_numpy(I).pin_memory()
+    dst = torch.from_numpy(J).pin_memory()
+    perm, so, do = boba.reorder_host(src, dst, n)
+    torch.cuda.synchronize()
+    boba.stream_status()
+    operm, oso, odo = oracle.reorder(I, J, n)
+    np.testing.assert_array_equal(perm.numpy(), operm)
+    np.testing.assert_array_equal(so.numpy(), oso)
+    np.testing.assert_array_equal(do.numpy(), odo)
