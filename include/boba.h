@@ -427,10 +427,8 @@ enum { BOBA_TUNE_FIRST = 0, BOBA_TUNE_RELABEL = 1, BOBA_TUNE_BATCHED = 2, BOBA_T
        BOBA_TUNE_CSR = 4 };
 
 /*
- * boba_tune_reorder -- times every variant (block size x loads in flight, and
- * the default shape with the n-sized key/label array held persisting in L2
- * through an access-policy window) of the first-occurrence kernel, then of
- * the relabel kernel, on this graph with
+ * boba_tune_reorder -- times every variant (block size x loads in flight) of
+ * the first-occurrence kernel, then of the relabel kernel, on this graph with
  * boba_reorder_ex's arguments, discards any variant whose perm/src_out/dst_out
  * differ from the default's in a single bit, and keeps the fastest for graphs
  * in the same power-of-two size class of m on this device.  chosen (int[2],

@@ -394,62 +394,9 @@ void launch_relabel_v(const ReorderArgs &a, cudaStream_t stream)
                                                               a.src_out, a.dst_out, a.status));
 }
 
-// Launch `kernel` with an L2 access-policy window that keeps the n-sized
-// key/label array resident (persisting) while the edge streams pass through.
-// The set-aside is a limit of this process's CUDA context (released with it).
-template <typename... Args>
-bool launch_persisting(void (*kernel)(Args...), int grid, int block, cudaStream_t s,
-                       const void *hot, size_t hot_bytes, Args... args)
-{
-    static bool limit_set[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
-    int max_persist = 0, max_window = 0;
-    cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev);
-    cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev);
-    if (max_persist <= 0 || max_window <= 0) {
-        (void)cudaGetLastError();
-        return false;
-    }
-    if (!limit_set[dev]) {
-        if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)max_persist) != cudaSuccess) {
-            (void)cudaGetLastError();
-            return false;
-        }
-        limit_set[dev] = true;
-    }
-    cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeAccessPolicyWindow;
-    attr.val.accessPolicyWindow.base_ptr = const_cast<void *>(hot);
-    attr.val.accessPolicyWindow.num_bytes = hot_bytes < (size_t)max_window ? hot_bytes : (size_t)max_window;
-    attr.val.accessPolicyWindow.hitRatio =
-        hot_bytes <= (size_t)max_persist ? 1.0f : (float)max_persist / (float)hot_bytes;
-    attr.val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
-    attr.val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, args...) == cudaSuccess;
-}
-
-// Variant table: index -> (block, loads in flight).  Index 0 is the default;
-// 6 is the default shape with the key array held persisting in L2.
+// Variant table: index -> (block, loads in flight).  Index 0 is the default.
 bool launch_first_variant(int v, const ReorderArgs &a, cudaStream_t s)
 {
-    if (v == 6) {
-        const int64_t work = cdiv(2 * a.m, 4LL * kFirstBlock * kFirstUnroll);
-        const int g = persistent_grid((const void *)k_first<true>, kFirstBlock, work);
-        bool ok = false;
-        BOBA_TIMED("reorder.first", s,
-                   ok = launch_persisting(k_first<true>, g, kFirstBlock, s, (const void *)a.key,
-                                          (size_t)a.n * 4, a.src, a.dst, a.m, a.n, a.key, a.status));
-        if (!ok) (void)cudaGetLastError();
-        return ok;
-    }
     switch (v) {
     case 1: launch_first_v<256, 2>(a, s); return true;
     case 2: launch_first_v<256, 8>(a, s); return true;
@@ -462,18 +409,6 @@ bool launch_first_variant(int v, const ReorderArgs &a, cudaStream_t s)
 
 bool launch_relabel_variant(int v, const ReorderArgs &a, cudaStream_t s)
 {
-    if (v == 6) {
-        const int64_t work = cdiv(2 * a.m, 4LL * kRelabelBlock * kRelabelUnroll);
-        const int g = persistent_grid((const void *)k_relabel<true>, kRelabelBlock, work);
-        bool ok = false;
-        const int32_t *lab = a.label;
-        BOBA_TIMED("reorder.relabel", s,
-                   ok = launch_persisting(k_relabel<true>, g, kRelabelBlock, s, (const void *)lab,
-                                          (size_t)a.n * 4, a.src, a.dst, a.m, a.n, lab, a.src_out,
-                                          a.dst_out, a.status));
-        if (!ok) (void)cudaGetLastError();
-        return ok;
-    }
     switch (v) {
     case 1: launch_relabel_v<256, 2>(a, s); return true;
     case 2: launch_relabel_v<256, 8>(a, s); return true;
