@@ -412,6 +412,16 @@ size_t boba_nbr_workspace_bytes(int64_t n_rows, int64_t nnz);
  */
 boba_status_t boba_stream_status(void *stream);
 
+/*
+ * boba_selftest_wait_timeout -- exercises the bounded spin-wait that every
+ * single-pass scan of this library uses: one warp waits for a predecessor
+ * whose flag nothing ever sets, gives up after timeout_ns (1 .. 2e9), records
+ * BOBA_ERR_TIMEOUT in the status word and returns, leaving the context
+ * usable.  scratch: 24 bytes of device memory.  Read the result with
+ * boba_stream_status().  (A diagnostic; the paper has no counterpart.)
+ */
+boba_status_t boba_selftest_wait_timeout(uint64_t timeout_ns, void *scratch, void *stream);
+
 /* boba_status_string -- a static, human-readable name for a status code. */
 const char *boba_status_string(boba_status_t status);
 

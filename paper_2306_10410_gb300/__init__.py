@@ -226,6 +226,10 @@ def boba_version():
     return load().boba_version().decode()
 
 
+def boba_selftest_wait_timeout(timeout_ns, scratch, stream=None):
+    return load().boba_selftest_wait_timeout(int(timeout_ns), _p(scratch), _s(stream))
+
+
 def boba_stream_status(stream=None):
     return load().boba_stream_status(_s(stream))
 

@@ -73,9 +73,35 @@ int persistent_grid(const void *kernel, int block, int64_t max_blocks, size_t dy
     return (int)g;
 }
 
+// Self-test of the bounded wait: tile 1 looks back at tile 0, whose status
+// word nothing ever publishes (it stays 0).  The wait must give up after
+// timeout_ns, record BOBA_ERR_TIMEOUT and let the kernel finish.
+__global__ void k_selftest_lookback(uint64_t *tstat, uint32_t *status, uint64_t timeout_ns,
+                                    uint64_t *out)
+{
+    if (threadIdx.x < 32) {
+        const uint64_t p = lookback_exclusive(tstat, 1, 5, status, false, timeout_ns);
+        if (threadIdx.x == 0) *out = p;
+    }
+}
+
 }  // namespace boba
 
 using namespace boba;
+
+extern "C" boba_status_t boba_selftest_wait_timeout(uint64_t timeout_ns, void *scratch,
+                                                    void *stream)
+{
+    if (scratch == nullptr || timeout_ns == 0 || timeout_ns > kTimeoutNs) return BOBA_ERR_INVALID_ARG;
+    const DeviceInfo *d = device_info();
+    if (!d) return BOBA_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uint64_t *tstat = static_cast<uint64_t *>(scratch);
+    BOBA_CUDA_TRY(cudaMemsetAsync(tstat, 0, 3 * sizeof(uint64_t), s));
+    k_selftest_lookback<<<1, 32, 0, s>>>(tstat, d->status, timeout_ns, tstat + 2);
+    BOBA_LAUNCH_CHECK();
+    return BOBA_OK;
+}
 
 extern "C" boba_status_t boba_reorder(const int32_t *src, const int32_t *dst, int64_t m,
                                       int64_t n, int32_t *perm_out, int32_t *src_out,

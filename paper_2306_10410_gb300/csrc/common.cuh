@@ -123,6 +123,7 @@ constexpr uint64_t kFlagPre = 2ull << 62;
 constexpr uint64_t kFlagMask = 3ull << 62;
 constexpr uint64_t kValMask = ~kFlagMask;
 constexpr uint64_t kTimeoutNs = 2000000000ull;   // 2 s
+constexpr uint32_t kMaxSpins = 1u << 26;          // second bound, independent of the timer
 
 struct OpSum {
     __device__ __forceinline__ static uint64_t apply(uint64_t a, uint64_t b) { return a + b; }
@@ -138,7 +139,8 @@ struct OpMax {
 // prefix at once, and no look-back walks past it (segmented scans).
 template <class Op = OpSum>
 __device__ __forceinline__ uint64_t lookback_exclusive(uint64_t *tstat, int64_t tile, uint64_t agg,
-                                                       uint32_t *status, bool seg_first = false)
+                                                       uint32_t *status, bool seg_first = false,
+                                                       uint64_t timeout_ns = kTimeoutNs)
 {
     const int lane = threadIdx.x & 31;
     if (tile == 0 || seg_first) {
@@ -159,11 +161,11 @@ __device__ __forceinline__ uint64_t lookback_exclusive(uint64_t *tstat, int64_t 
             if (__all_sync(kFull, (s & kFlagMask) != 0)) break;
             if (timed_out) { if ((s & kFlagMask) == 0) s = kFlagPre; break; }
             ++spins;
-            if ((spins & 255u) == 1u) {
+            if ((spins & 255u) == 1u || spins >= kMaxSpins) {
                 // lane 0's clock, broadcast, keeps the decision warp-uniform
                 const uint64_t now = __shfl_sync(kFull, globaltimer_ns(), 0);
                 if (t0 == 0) t0 = now;
-                else if (now - t0 > kTimeoutNs) {
+                if (now - t0 > timeout_ns || spins >= kMaxSpins) {
                     if (lane == 0) raise_status(status, BOBA_ERR_TIMEOUT);
                     timed_out = true;
                 }

@@ -236,10 +236,10 @@ __global__ void __launch_bounds__(BLOCK) k_csr_pass(
                 if (done) break;
                 t -= used;
                 if (used == 0) {
-                    if ((++spins & 255u) == 1u) {
+                    if ((++spins & 255u) == 1u || spins >= kMaxSpins) {
                         const uint64_t now = globaltimer_ns();
                         if (tstart == 0) tstart = now;
-                        else if (now - tstart > kTimeoutNs) {
+                        if (now - tstart > kTimeoutNs || spins >= kMaxSpins) {
                             raise_status(status, BOBA_ERR_TIMEOUT);
                             break;
                         }
