@@ -20,6 +20,8 @@ of the paper it follows:
 * :func:`nbr`          -- the NBR line metric (Sec. 5.2)
 * :func:`sort_by_dst`  -- the edge list stably sorted or binned by destination,
                           the remedy for random edge order (Sec. 5.6)
+* :func:`pagerank`     -- the PR application of Sec. 5.1, power iteration in
+                          fp64 with the standard damping and dangling terms
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (paper worked examples, brute force, closed forms, invariants).
@@ -49,7 +51,7 @@ def build(force: bool = False) -> str:
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11",
-                           "-fno-fast-math", "-o", tmp, _SRC])
+                           "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
     os.replace(tmp, _LIB)
     return _LIB
 
@@ -73,6 +75,9 @@ def _load():
                 f = getattr(lib, name)
                 f.argtypes = args
                 f.restype = ctypes.c_int
+            lib.oracle_pagerank.argtypes = [p, p, i64, i64, ctypes.c_double, i64,
+                                             ctypes.c_double, p, p, p]
+            lib.oracle_pagerank.restype = ctypes.c_int
             lib.oracle_nbr.argtypes = [p, p, i64, i64, p]
             lib.oracle_nbr.restype = ctypes.c_double
             _lib = lib
@@ -201,3 +206,17 @@ def sort_by_dst(I, J, n: int, top_digit_only: bool = False):
         key = (key >> max(0, bits - 8)) & 255
     order = np.argsort(key, kind="stable")
     return I[order], J[order]
+
+
+def pagerank(I, J, n: int, damping: float = 0.85, max_iters: int = 100, tol: float = 0.0):
+    """(pr, steps, residual): PageRank of the edge list by fp64 power iteration
+    (Sec. 5.1 applications; standard damping and uniform dangling mass)."""
+    I, J = _i32(I), _i32(J)
+    m = I.shape[0]
+    pr = np.empty(max(n, 0), dtype=np.float64)
+    it = ctypes.c_int64(0)
+    res = ctypes.c_double(0.0)
+    _check(_load().oracle_pagerank(_ptr(I), _ptr(J), m, n, float(damping), int(max_iters),
+                                   float(tol), _ptr(pr), ctypes.byref(it), ctypes.byref(res)),
+           "pagerank")
+    return pr, int(it.value), float(res.value)

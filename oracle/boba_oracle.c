@@ -16,6 +16,7 @@
  *
  * Return codes: 0 ok, 1 invalid argument, 2 a vertex ID outside [0, n).
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -225,4 +226,52 @@ double oracle_nbr(const int64_t *row_ptr, const int32_t *col, int64_t n_rows,
     free(buf);
     if (n_counted) *n_counted = counted;
     return counted ? sum / (double)counted : 0.0;
+}
+
+/*
+ * PageRank by power iteration over the edge list, the PR application of
+ * Sec. 5.1 (it sweeps the whole graph repeatedly until convergence).  The paper
+ * fixes none of its constants, so this is the standard definition (Page, Brin,
+ * Motwani, Winograd 1999) in fp64, dangling mass spread uniformly:
+ *   pr_0(v)     = 1/n
+ *   D_t         = sum of pr_t(u) over the vertices u with outdeg(u) = 0
+ *   pr_{t+1}(v) = (1 - d)/n + d * ( sum over edges u -> v of pr_t(u)/outdeg(u) + D_t/n )
+ * outdeg counts duplicated edges; a self-loop is an ordinary edge.  Steps until
+ * sum_v |pr_{t+1}(v) - pr_t(v)| < tol or max_iters steps have been taken.
+ * pr (length n) receives the last iterate; *iters the steps taken and
+ * *residual the last step's L1 change (0 if no step was taken).
+ */
+int oracle_pagerank(const int32_t *I, const int32_t *J, int64_t m, int64_t n, double d,
+                    int64_t max_iters, double tol, double *pr, int64_t *iters, double *residual)
+{
+    if (m < 0 || n < 0 || (m > 0 && n == 0) || max_iters < 0 || !(d >= 0.0 && d < 1.0))
+        return 1;
+    if (check_ids(I, m, n) || check_ids(J, m, n)) return 2;
+    *iters = 0;
+    *residual = 0.0;
+    if (n == 0) return 0;
+    int64_t *outdeg = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+    double *next = (double *)malloc((size_t)n * sizeof(double));
+    if (!outdeg || !next) { free(outdeg); free(next); return 1; }
+    for (int64_t e = 0; e < m; ++e) outdeg[I[e]] += 1;
+    for (int64_t v = 0; v < n; ++v) pr[v] = 1.0 / (double)n;
+    for (int64_t t = 0; t < max_iters; ++t) {
+        double dangling = 0.0;
+        for (int64_t u = 0; u < n; ++u)
+            if (outdeg[u] == 0) dangling += pr[u];
+        for (int64_t v = 0; v < n; ++v) next[v] = 0.0;
+        for (int64_t e = 0; e < m; ++e) next[J[e]] += pr[I[e]] / (double)outdeg[I[e]];
+        double change = 0.0;
+        for (int64_t v = 0; v < n; ++v) {
+            double nv = (1.0 - d) / (double)n + d * (next[v] + dangling / (double)n);
+            change += fabs(nv - pr[v]);
+            pr[v] = nv;
+        }
+        *iters = t + 1;
+        *residual = change;
+        if (change < tol) break;
+    }
+    free(outdeg);
+    free(next);
+    return 0;
 }

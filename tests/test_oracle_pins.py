@@ -314,3 +314,113 @@ def test_sort_by_dst_pins():
     for d in range(0, 256, 37):
         sel = top(J) == d
         assert np.array_equal(Ib[top(Jb) == d], I[sel]) and np.array_equal(Jb[top(Jb) == d], J[sel])
+
+
+# --- PageRank (Sec. 5.1 applications) -------------------------------------------
+
+def google_matrix(I, J, n, d):
+    """The dense Google matrix, entry by entry: column u spreads pr(u) over u's
+    out-edges (duplicates counted), or over all n vertices when u has none."""
+    outdeg = np.bincount(np.asarray(I, dtype=np.int64), minlength=n)
+    G = np.zeros((n, n))
+    for u, v in zip(I, J):
+        G[v, u] += 1.0 / outdeg[u]
+    for u in range(n):
+        if outdeg[u] == 0:
+            G[:, u] = 1.0 / n
+    return d * G + (1.0 - d) / n
+
+
+def stationary(G):
+    """The eigenvector of G for the eigenvalue nearest 1, scaled to sum 1."""
+    w, V = np.linalg.eig(G)
+    k = int(np.argmin(np.abs(w - 1.0)))
+    assert abs(w[k] - 1.0) < 1e-9
+    v = np.real(V[:, k])
+    return v / v.sum()
+
+
+def random_small_graph(rng, n, m):
+    I = rng.integers(0, n, m).astype(np.int32)
+    J = rng.integers(0, n, m).astype(np.int32)
+    return I, J
+
+
+@pytest.mark.parametrize("d", [0.0, 0.5, 0.85, 0.95])
+def test_pagerank_two_vertex_closed_form(d):
+    """One edge 0 -> 1 (vertex 1 dangling): pr = (1/(2+d), (1+d)/(2+d))."""
+    pr, steps, res = oracle.pagerank([0], [1], 2, d, 10000, 1e-15)
+    np.testing.assert_allclose(pr, [1 / (2 + d), (1 + d) / (2 + d)], rtol=0, atol=1e-13)
+    assert res < 1e-15
+
+
+def test_pagerank_cycle_is_uniform():
+    n = 9
+    I = np.arange(n, dtype=np.int32)
+    J = (I + 1) % n
+    pr, steps, res = oracle.pagerank(I, J, n, 0.85, 50)
+    np.testing.assert_allclose(pr, np.full(n, 1 / n), rtol=0, atol=1e-15)
+    assert steps == 50 and res < 1e-15
+
+
+def test_pagerank_is_the_google_eigenvector():
+    """Converged power iteration equals the stationary vector of the dense Google
+    matrix, found by an eigen-decomposition (dangling vertices, duplicated edges
+    and self-loops included)."""
+    rng = np.random.default_rng(2024)
+    for trial in range(40):
+        n = int(rng.integers(1, 13))
+        m = int(rng.integers(0, 3 * n + 1))
+        I, J = random_small_graph(rng, n, m)
+        d = float(rng.choice([0.3, 0.85, 0.9]))
+        pr, steps, res = oracle.pagerank(I, J, n, d, 100000, 1e-15)
+        np.testing.assert_allclose(pr, stationary(google_matrix(I, J, n, d)), rtol=0,
+                                   atol=1e-11, err_msg=f"trial {trial}")
+
+
+def test_pagerank_mass_and_special_cases():
+    rng = np.random.default_rng(5)
+    I, J = random_small_graph(rng, 30, 40)            # many dangling vertices
+    for t in range(6):
+        pr, steps, res = oracle.pagerank(I, J, 30, 0.85, t)
+        assert steps == t
+        assert abs(pr.sum() - 1.0) < 1e-13            # mass is conserved every step
+        if t == 0:
+            np.testing.assert_array_equal(pr, np.full(30, 1 / 30))
+    pr, _, _ = oracle.pagerank(I, J, 30, 0.0, 1)      # no damping weight on edges
+    np.testing.assert_allclose(pr, np.full(30, 1 / 30), rtol=0, atol=1e-16)
+    pr, _, _ = oracle.pagerank([], [], 7, 0.85, 10)   # no edges: everything dangling
+    np.testing.assert_allclose(pr, np.full(7, 1 / 7), rtol=0, atol=1e-16)
+    pr, _, _ = oracle.pagerank([0, 0], [0, 0], 1, 0.85, 10)
+    np.testing.assert_allclose(pr, [1.0], rtol=0, atol=1e-15)
+    with pytest.raises(oracle.OracleError):
+        oracle.pagerank([0], [2], 2, 0.85, 5)
+    with pytest.raises(oracle.OracleError):
+        oracle.pagerank([0], [1], 2, 1.0, 5)
+
+
+def test_pagerank_planted_mistakes_fail_the_eigen_pin():
+    """Plausible slips in a power iteration (dropped dangling term, normalising by
+    in-degree, transposed edges) all miss the eigenvector pin."""
+    rng = np.random.default_rng(11)
+    n, d = 12, 0.85
+    I, J = random_small_graph(rng, n, 20)
+    I[0], J[0] = 3, 3
+    want = stationary(google_matrix(I, J, n, d))
+
+    def power(I, J, deg, dangling):
+        pr = np.full(n, 1 / n)
+        for _ in range(500):
+            nxt = np.zeros(n)
+            for u, v in zip(I, J):
+                nxt[v] += pr[u] / deg[u]
+            D = pr[deg == 0].sum() if dangling else 0.0
+            pr = (1 - d) / n + d * (nxt + D / n)
+        return pr
+
+    outdeg = np.bincount(I, minlength=n)
+    indeg = np.bincount(J, minlength=n)
+    np.testing.assert_allclose(power(I, J, outdeg, True), want, atol=1e-11)
+    assert np.abs(power(I, J, outdeg, False) - want).max() > 1e-3
+    assert np.abs(power(I, J, np.maximum(indeg, 1), True) - want).max() > 1e-3
+    assert np.abs(power(J, I, np.bincount(J, minlength=n), True) - want).max() > 1e-3
