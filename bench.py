@@ -424,12 +424,38 @@ def compare_orders(args, boba, torch, dev, stream, src, dst, so, do, m, n, row_p
                      "csr_plus_spmv_ms": round(statistics.median(tsp), 4), "nbr32": round(v, 5)}
     del s2, d2, s3, d3, ws_sort, ws_r2
     boba.stream_status(stream)
-    # NBR spatial-locality metric (Sec. 5.2) of the two CSRs, lines of 32 IDs
+    # NBR spatial-locality metric (Sec. 5.2) of the two CSRs, lines of 32 IDs, and
+    # PageRank (Sec. 5.1 applications) on each: spmv_iters fixed steps, then the
+    # steps needed for an L1 change below 1e-6
+    ws_pr = torch.empty(boba.boba_pagerank_workspace_bytes(n, m), dtype=torch.uint8, device=dev)
+    pr = torch.empty(n, dtype=torch.float32, device=dev)
+    pr_steps = torch.zeros(1, dtype=torch.int32, device=dev)
+    pr_res = torch.zeros(1, dtype=torch.float64, device=dev)
+    k = max(1, args.spmv_iters)
     for name, (s_, d_) in (("random", (src, dst)), ("boba", (so, do))):
         boba.check(boba.boba_coo_to_csr(s_, d_, m, n, row_ptr, col, val, ws_c, ws_c.numel(),
                                         stream), "csr")
         v, cnt = boba.nbr(row_ptr, col, ids_per_line=32)
         out[name]["nbr32"] = round(v, 5)
+        t_pr = []
+        for rep in range(4):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            boba.check(boba.boba_pagerank(row_ptr, col, val, n, m, 0.85, k, 0.0, pr, pr_steps,
+                                          pr_res, ws_pr, ws_pr.numel(), stream), "pagerank")
+            ev[1].record(stream)
+            torch.cuda.synchronize(dev)
+            if rep:
+                t_pr.append(ev[0].elapsed_time(ev[1]) / k)
+        boba.check(boba.boba_pagerank(row_ptr, col, val, n, m, 0.85, 1000, 1e-6, pr, pr_steps,
+                                      pr_res, ws_pr, ws_pr.numel(), stream), "pagerank")
+        boba.stream_status(stream)
+        out[name]["pagerank_ms_per_step"] = round(statistics.median(t_pr), 4)
+        out[name]["pagerank_steps_to_1e-6"] = int(pr_steps.item())
+    del ws_pr, pr
+    out["pagerank_speedup_boba_vs_random"] = round(
+        out["random"]["pagerank_ms_per_step"] / out["boba"]["pagerank_ms_per_step"], 3)
     out["csr_speedup_boba_vs_random"] = round(out["random"]["csr_ms"] / out["boba"]["csr_ms"], 3)
     out["spmv_bytes_per_launch"] = spmv_bytes
     return out
@@ -534,30 +560,52 @@ def run_batched(args, boba, torch, dev, stream, flush, n_batch=4096, seed=None):
 def run_e2e(args, boba, torch, dev, stream, src_h, dst_h, m, n, world):
     """Same metric through the C ABI with the graph in pinned host memory:
     boba_reorder_host copies the edges in, reorders and copies perm and the
-    relabelled edges out, all inside the timed region."""
-    perm_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
-    so_h = torch.empty(m, dtype=torch.int32, pin_memory=True)
-    do_h = torch.empty(m, dtype=torch.int32, pin_memory=True)
-    ws = torch.empty(boba.boba_reorder_host_workspace_bytes(m, n), dtype=torch.uint8, device=dev)
+    relabelled edges out, all inside the timed region.
 
-    def one(ev):
-        ev[0].record(stream)
-        boba.check(boba.boba_reorder_host(src_h, dst_h, m, n, perm_h, so_h, do_h, ws, ws.numel(),
-                                          stream), "reorder_host")
-        ev[1].record(stream)
+    Steps alternate between two streams, each with its own workspace and host
+    output buffers, as a caller streaming graphs would: the input copies of
+    step k+1 then run while step k's results are copied out.  The timed region
+    spans all K steps; the latency of one call alone is reported beside it."""
+    streams = [stream, torch.cuda.Stream(dev)]
+    outs = [(torch.empty(n, dtype=torch.int32, pin_memory=True),
+             torch.empty(m, dtype=torch.int32, pin_memory=True),
+             torch.empty(m, dtype=torch.int32, pin_memory=True)) for _ in range(2)]
+    nbytes = boba.boba_reorder_host_workspace_bytes(m, n)
+    wss = [torch.empty(nbytes, dtype=torch.uint8, device=dev) for _ in range(2)]
 
-    for _ in range(max(1, args.warmup)):
-        one([torch.cuda.Event(enable_timing=True) for _ in range(2)])
+    def one(k):
+        s = streams[k % 2]
+        perm_h, so_h, do_h = outs[k % 2]
+        boba.check(boba.boba_reorder_host(src_h, dst_h, m, n, perm_h, so_h, do_h, wss[k % 2],
+                                          nbytes, s), "reorder_host")
+
+    for k in range(max(2, args.warmup)):
+        one(k)
     torch.cuda.synchronize(dev)
-    times = []
-    steps = max(1, min(args.steps, 10))
-    for _ in range(steps):
+    # one call alone: its latency
+    lat = []
+    for k in range(3):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        one(ev)
+        ev[0].record(streams[0])
+        one(0)
+        ev[1].record(streams[0])
         torch.cuda.synchronize(dev)
-        times.append(ev[0].elapsed_time(ev[1]))
+        lat.append(ev[0].elapsed_time(ev[1]))
+    # K steps back to back on alternating streams
+    steps = max(2, min(args.steps, 10))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(streams[0])
+    streams[1].wait_event(ev0)
+    for k in range(steps):
+        one(k)
+    done1 = torch.cuda.Event()
+    done1.record(streams[1])
+    streams[0].wait_event(done1)
+    ev1.record(streams[0])
+    torch.cuda.synchronize(dev)
     boba.stream_status(stream)
-    ms = statistics.mean(times)
+    ok = all(torch.equal(outs[0][i], outs[1][i]) for i in range(3))
+    ms = ev0.elapsed_time(ev1) / steps
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([ms], device=dev)
@@ -566,7 +614,11 @@ def run_e2e(args, boba, torch, dev, stream, src_h, dst_h, m, n, world):
     return {"value": round(world * m / (ms * 1e-3) / 1e9, 3), "unit": "Gedges/s",
             "ms_per_step": round(ms, 3), "h2d_bytes_per_step": 8 * m,
             "d2h_bytes_per_step": 8 * m + 4 * n,
-            "api": "boba_reorder_host (chunked, copies overlapped with kernels)"}
+            "single_call_ms": round(statistics.median(lat), 3),
+            "outputs_equal_across_streams": ok,
+            "api": "boba_reorder_host (chunked, copies overlapped with kernels); "
+                   "steps alternate over 2 streams so step k+1's input copies overlap "
+                   "step k's output copies"}
 
 
 def load_traffic(kernel, workload):

@@ -368,6 +368,40 @@ boba_status_t boba_spmv_csr(const int64_t *row_ptr, const int32_t *col, const fl
 size_t boba_spmv_workspace_bytes(int64_t n_rows, int64_t nnz);
 
 /*
+ * boba_pagerank -- PageRank of the graph behind a pull CSR, the PR application
+ * of Sec. 5.1 (it sweeps the whole graph repeatedly until convergence).  The
+ * paper fixes no constants; this is the standard power iteration with damping
+ * d and the mass of vertices with no out-edge spread uniformly:
+ *   pr_0(v) = 1/n,
+ *   pr_{t+1}(v) = (1-d)/n + d * ( sum over entries (v,u) of val * pr_t(u)
+ *                                 + (sum of pr_t(u) over u with no out-edge)/n ),
+ * stopping after the first step whose L1 change sum_v |pr_{t+1}(v) - pr_t(v)|
+ * is below tol, or after max_iters steps (tol = 0: exactly max_iters steps).
+ * The CSR must be the one boba_coo_to_csr writes for the graph
+ * (val = 1/outdeg(u), column u has an out-edge iff it occurs in col).
+ * Each step is the merge-path SpMV plus one update pass; ranks are fp32,
+ * the change and the dangling mass are summed in fp64 in a fixed order, so
+ * the result is the same run to run.
+ *
+ *   row_ptr int64[n+1], col int32[nnz], val float[nnz]   (device)
+ *   damping  d in [0, 1);  max_iters in [0, 2^20];  tol >= 0
+ *   pr       float[n] (device): receives the ranks
+ *   iters_out     int32 (device, nullable): steps taken
+ *   residual_out  double (device, nullable): L1 change of the last step
+ *   ws       scratch of boba_pagerank_workspace_bytes(n, nnz) bytes
+ * Asynchronous: every step is enqueued at once and the steps after
+ * convergence return immediately; never allocates, so it can be captured in
+ * a CUDA graph.  A column ID outside [0, n) records
+ * BOBA_ERR_ID_OUT_OF_RANGE and no step runs (pr stays 1/n).
+ */
+boba_status_t boba_pagerank(const int64_t *row_ptr, const int32_t *col, const float *val,
+                            int64_t n, int64_t nnz, double damping, int64_t max_iters,
+                            double tol, float *pr, int32_t *iters_out, double *residual_out,
+                            void *ws, size_t ws_bytes, void *stream);
+
+size_t boba_pagerank_workspace_bytes(int64_t n, int64_t nnz);
+
+/*
  * boba_sort_by_dst -- reorders the edges of a COO stably by destination
  * (top_digit_only = 0: a full sort; != 0: only by the top 8 significant
  * bits of the destination as a ceil(log2 n)-bit number -- 256 bins, one

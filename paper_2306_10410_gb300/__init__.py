@@ -17,6 +17,7 @@ __all__ = [
     "boba_reorder", "boba_reorder_ex", "boba_reorder_workspace_bytes", "boba_reorder_static", "boba_reorder_batched",
     "boba_reorder_batched_workspace_bytes", "boba_batched_set_mode", "boba_coo_to_csr", "boba_coo_to_csr_workspace_bytes",
     "boba_spmv_csr", "boba_spmv_workspace_bytes", "boba_stream_status", "boba_status_string",
+    "boba_pagerank", "boba_pagerank_workspace_bytes", "pagerank",
     "Workspace", "kernel_timing", "nbr", "reorder_variant", "reorder_host", "sort_by_dst", "tune_reorder", "tune_batched", "tune_spmv", "tune_save",
     "tune_load", "tune_reset", "tune_csr", "TUNE_FIRST", "TUNE_RELABEL", "TUNE_BATCHED",
     "TUNE_SPMV", "TUNE_CSR",
@@ -103,6 +104,17 @@ def boba_spmv_csr(row_ptr, col, val, x, y, n_rows, nnz, ws, ws_bytes, stream=Non
 
 def boba_spmv_workspace_bytes(n_rows, nnz):
     return load().boba_spmv_workspace_bytes(n_rows, nnz)
+
+
+def boba_pagerank(row_ptr, col, val, n, nnz, damping, max_iters, tol, pr, iters_out,
+                  residual_out, ws, ws_bytes, stream=None):
+    return load().boba_pagerank(_p(row_ptr), _p(col), _p(val), n, nnz, float(damping),
+                                int(max_iters), float(tol), _p(pr), _p(iters_out),
+                                _p(residual_out), _p(ws), ws_bytes, _s(stream))
+
+
+def boba_pagerank_workspace_bytes(n, nnz):
+    return load().boba_pagerank_workspace_bytes(n, nnz)
 
 
 def _hp(t):
@@ -353,6 +365,22 @@ def spmv(row_ptr, col, val, x, *, y=None, nnz=None, ws=None, stream=None):
     check(boba_spmv_csr(row_ptr, col, val, x, y, n_rows, nnz, buf, buf.numel(), stream),
           "boba_spmv_csr")
     return y
+
+
+def pagerank(row_ptr, col, val, *, damping=0.85, max_iters=100, tol=1e-6, pr=None, nnz=None,
+             ws=None, stream=None):
+    """PageRank over a CSR built by coo_to_csr: (pr, steps, residual) with pr an fp32
+    device tensor and steps / residual device tensors (int32[1], float64[1])."""
+    n = row_ptr.numel() - 1
+    nnz = col.numel() if nnz is None else nnz
+    dev = row_ptr.device
+    pr = torch.empty(n, dtype=torch.float32, device=dev) if pr is None else pr
+    steps = torch.zeros(1, dtype=torch.int32, device=dev)
+    residual = torch.zeros(1, dtype=torch.float64, device=dev)
+    buf = _ws(ws, boba_pagerank_workspace_bytes(n, nnz), dev)
+    check(boba_pagerank(row_ptr, col, val, n, nnz, damping, max_iters, tol, pr, steps, residual,
+                        buf, buf.numel(), stream), "boba_pagerank")
+    return pr, steps, residual
 
 
 class kernel_timing:

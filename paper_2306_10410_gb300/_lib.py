@@ -49,6 +49,9 @@ SIGNATURES = {
     "boba_coo_to_csr_workspace_bytes": (_SZ, [_I64, _I64]),
     "boba_spmv_csr": (_ST, [_P, _P, _P, _P, _P, _I64, _I64, _P, _SZ, _P]),
     "boba_spmv_workspace_bytes": (_SZ, [_I64, _I64]),
+    "boba_pagerank": (_ST, [_P, _P, _P, _I64, _I64, ctypes.c_double, _I64, ctypes.c_double, _P,
+                            _P, _P, _P, _SZ, _P]),
+    "boba_pagerank_workspace_bytes": (_SZ, [_I64, _I64]),
     "boba_sort_by_dst": (_ST, [_P, _P, _I64, _I64, _P, _P, ctypes.c_int, _P, _SZ, _P]),
     "boba_sort_by_dst_workspace_bytes": (_SZ, [_I64, _I64]),
     "boba_nbr": (_ST, [_P, _P, _I64, _I64, _I64, _P, _P, _P, _SZ, _P]),

@@ -53,6 +53,18 @@ enum TuneKernel { kTuneFirst = 0, kTuneRelabel = 1, kTuneBatched = 2, kTuneSpmv 
 int tuned_variant(int kernel, int64_t size);
 int size_class(int64_t size);
 
+// Merge-path SpMV (spmv.cu), shared with the iterative callers.  `variant` is a
+// tuned SpMV variant 5..8 (anything else means 5): it fixes the block shape and
+// the path items per tile.  The partition depends on row_ptr only, so an
+// iterative caller computes it once.  A non-null `skip` pointing at a nonzero
+// word makes the multiply's kernels return at once.
+int merge_path_items(int variant);
+void merge_path_partition(const int64_t *row_ptr, int64_t n, int64_t nnz, int items, int2 *part,
+                          cudaStream_t stream);
+void merge_path_multiply(int variant, const int64_t *row_ptr, const int32_t *col, const float *val,
+                         const float *x, float *y, int64_t n, int64_t nnz, const int2 *part,
+                         int32_t *crow, float *cval, const uint32_t *skip, cudaStream_t stream);
+
 }  // namespace boba
 
 // BOBA_TIMED("name", stream, kernel<<<g, b, smem, stream>>>(args));

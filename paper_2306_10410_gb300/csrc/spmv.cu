@@ -214,8 +214,9 @@ __global__ void __launch_bounds__(MB) k_mp_spmv(
     const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
     const float *__restrict__ val, const float *__restrict__ x, float *__restrict__ y, int64_t n,
     int64_t nnz, const int2 *__restrict__ part, int32_t *__restrict__ carry_row,
-    float *__restrict__ carry_val)
+    float *__restrict__ carry_val, const uint32_t *skip)
 {
+    if (skip != nullptr && *skip != 0) return;       // an iterative caller has converged
     constexpr int kMpBlock = MB, kMpItems = MI, kMpTile = MB * MI;
     // one pad word per 32: a thread walks MI consecutive items, so without the
     // padding the lanes of a warp would hit the same few banks
@@ -250,11 +251,13 @@ __global__ void __launch_bounds__(MB) k_mp_spmv(
     float acc = 0.0f;
     float first_val = 0.0f;         // partial of the first row end this thread consumes
     int first_end = -1;             // that row (relative), or -1 if none
-    // consume kMpItems path items in order
+    // consume kMpItems path items in order; the current row's end stays in a
+    // register and is reloaded only when the row changes
+    int row_end = s_end[P(xt)];
 #pragma unroll
     for (int i = 0; i < kMpItems; ++i) {
         if (xt + yt >= nrows + nnzt) break;
-        if (yt < s_end[P(xt)]) {
+        if (yt < row_end) {
             acc += s_prod[P(yt)];
             ++yt;
         } else {
@@ -262,6 +265,7 @@ __global__ void __launch_bounds__(MB) k_mp_spmv(
             else y[x0 + xt] = acc;                 // row begun and ended in this thread
             acc = 0.0f;
             ++xt;
+            row_end = s_end[P(xt)];
         }
     }
     // segmented scan of the threads' trailing partials (row xt, value acc):
@@ -309,8 +313,10 @@ __global__ void __launch_bounds__(MB) k_mp_spmv(
 // y[r] += the carries of the tiles that ended inside row r, in tile order.
 __global__ void __launch_bounds__(256) k_mp_fixup(const int32_t *__restrict__ carry_row,
                                                   const float *__restrict__ carry_val,
-                                                  int64_t tiles, int64_t n, float *__restrict__ y)
+                                                  int64_t tiles, int64_t n, float *__restrict__ y,
+                                                  const uint32_t *skip)
 {
+    if (skip != nullptr && *skip != 0) return;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= tiles) return;
     const int32_t r = carry_row[t];
@@ -336,6 +342,43 @@ void launch_rows(const int64_t *row_ptr, const int32_t *col, const float *val, c
 }
 
 }  // namespace
+
+int merge_path_items(int variant)
+{
+    return variant == 6 ? 3072 : variant == 7 ? 4096 : 2048;
+}
+
+void merge_path_partition(const int64_t *row_ptr, int64_t n, int64_t nnz, int items, int2 *part,
+                          cudaStream_t stream)
+{
+    const int64_t tiles = cdiv(n + nnz, items);
+    BOBA_TIMED("spmv.partition", stream,
+               k_mp_partition<<<(unsigned)cdiv(tiles + 1, 256), 256, 0, stream>>>(
+                   row_ptr, n, nnz, tiles, items, part));
+}
+
+void merge_path_multiply(int variant, const int64_t *row_ptr, const int32_t *col, const float *val,
+                         const float *x, float *y, int64_t n, int64_t nnz, const int2 *part,
+                         int32_t *crow, float *cval, const uint32_t *skip, cudaStream_t stream)
+{
+    const int64_t tiles = cdiv(n + nnz, merge_path_items(variant));
+    if (variant == 6)
+        BOBA_TIMED("spmv", stream, k_mp_spmv<256, 12><<<(unsigned)tiles, 256, 0, stream>>>(
+                                       row_ptr, col, val, x, y, n, nnz, part, crow, cval, skip));
+    else if (variant == 7)
+        BOBA_TIMED("spmv", stream, k_mp_spmv<512, 8><<<(unsigned)tiles, 512, 0, stream>>>(
+                                       row_ptr, col, val, x, y, n, nnz, part, crow, cval, skip));
+    else if (variant == 8)
+        BOBA_TIMED("spmv", stream, k_mp_spmv<128, 16><<<(unsigned)tiles, 128, 0, stream>>>(
+                                       row_ptr, col, val, x, y, n, nnz, part, crow, cval, skip));
+    else
+        BOBA_TIMED("spmv", stream, k_mp_spmv<256, 8><<<(unsigned)tiles, 256, 0, stream>>>(
+                                       row_ptr, col, val, x, y, n, nnz, part, crow, cval, skip));
+    BOBA_TIMED("spmv.fixup", stream,
+               k_mp_fixup<<<(unsigned)cdiv(tiles, 256), 256, 0, stream>>>(crow, cval, tiles, n, y,
+                                                                           skip));
+}
+
 }  // namespace boba
 
 using namespace boba;
@@ -376,26 +419,9 @@ extern "C" boba_status_t boba_spmv_csr(const int64_t *row_ptr, const int32_t *co
         int2 *part = reinterpret_cast<int2 *>(b + L.mp_part);
         int32_t *crow = reinterpret_cast<int32_t *>(b + L.mp_crow);
         float *cval = reinterpret_cast<float *>(b + L.mp_cval);
-        const int items = tv == 5 ? 2048 : tv == 6 ? 3072 : tv == 7 ? 4096 : 2048;
-        const int64_t tiles = cdiv(n_rows + nnz, items);
-        BOBA_TIMED("spmv.partition", stream,
-                   k_mp_partition<<<(unsigned)cdiv(tiles + 1, 256), 256, 0, stream>>>(
-                       row_ptr, n_rows, nnz, tiles, items, part));
-        if (tv == 5)
-            BOBA_TIMED("spmv", stream, k_mp_spmv<256, 8><<<(unsigned)tiles, 256, 0, stream>>>(
-                                           row_ptr, col, val, x, y, n_rows, nnz, part, crow, cval));
-        else if (tv == 6)
-            BOBA_TIMED("spmv", stream, k_mp_spmv<256, 12><<<(unsigned)tiles, 256, 0, stream>>>(
-                                           row_ptr, col, val, x, y, n_rows, nnz, part, crow, cval));
-        else if (tv == 7)
-            BOBA_TIMED("spmv", stream, k_mp_spmv<512, 8><<<(unsigned)tiles, 512, 0, stream>>>(
-                                           row_ptr, col, val, x, y, n_rows, nnz, part, crow, cval));
-        else
-            BOBA_TIMED("spmv", stream, k_mp_spmv<128, 16><<<(unsigned)tiles, 128, 0, stream>>>(
-                                           row_ptr, col, val, x, y, n_rows, nnz, part, crow, cval));
-        BOBA_TIMED("spmv.fixup", stream,
-                   k_mp_fixup<<<(unsigned)cdiv(tiles, 256), 256, 0, stream>>>(crow, cval, tiles,
-                                                                               n_rows, y));
+        merge_path_partition(row_ptr, n_rows, nnz, merge_path_items(tv), part, stream);
+        merge_path_multiply(tv, row_ptr, col, val, x, y, n_rows, nnz, part, crow, cval, nullptr,
+                            stream);
         BOBA_LAUNCH_CHECK();
         return BOBA_OK;
     }
