@@ -3,17 +3,18 @@
 // edge order, and the entry of edge u -> v holds fp32(1 / outdeg(u)).
 //
 // A stable LSD radix sort of (key = dst, value = src) with 8-bit digits:
-//   k_csr_hist      per-digit histograms of all passes in one read of dst, and
-//                   outdeg(u) by atomic increments over src
+//   k_csr_hist      per-digit histograms of all passes in one read of dst
 //   k_csr_digits    exclusive scan of each pass's 256 digit counts
 //   k_csr_pass      one pass: stable in-tile ranking (warp match + per-warp
 //                   digit counters, items striped so processing order is input
 //                   order), per-digit decoupled look-back across tiles, and a
 //                   scatter staged through shared memory so that runs of equal
 //                   digits are written contiguously (Adinets and Merrill,
-//                   "Onesweep", 2022, for the single-pass scheme)
+//                   "Onesweep", 2022, for the single-pass scheme); the first
+//                   pass also counts outdeg(u) over the sources it carries
 //   k_csr_ends      ends[k] = one past the last sorted entry of row k, and
-//                   val = fp32(1 / outdeg(col))
+//                   val = fp32(1 / outdeg(col)); with two or more passes the
+//                   last pass does this itself as it writes its output
 //   k_csr_rowptr    row_ptr[v+1] = max over u <= v of ends[u] (a single-pass
 //                   max-scan with decoupled look-back), row_ptr[0] = 0
 #include "common.cuh"
@@ -82,11 +83,10 @@ __global__ void __launch_bounds__(256) k_zero(uint4 *p, int64_t n16)
         p[i] = z;
 }
 
-// Digit histograms of every pass over dst, plus outdeg over src.
-__global__ void __launch_bounds__(256) k_csr_hist(const int32_t *__restrict__ src,
-                                                  const int32_t *__restrict__ dst, int64_t m,
-                                                  uint32_t n, int passes, uint32_t *outdeg,
-                                                  uint32_t *hist, uint32_t *status)
+// Digit histograms of every pass over dst.
+__global__ void __launch_bounds__(256) k_csr_hist(const int32_t *__restrict__ dst, int64_t m,
+                                                  uint32_t n, int passes, uint32_t *hist,
+                                                  uint32_t *status)
 {
     __shared__ uint32_t sh[kMaxPasses * 256];
     for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) sh[i] = 0;
@@ -94,10 +94,7 @@ __global__ void __launch_bounds__(256) k_csr_hist(const int32_t *__restrict__ sr
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
         const uint32_t k = (uint32_t)ld_stream(dst + e);
-        const uint32_t s = (uint32_t)ld_stream(src + e);
         for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * 256 + ((k >> (8 * p)) & 255u)], 1u);
-        if (s < n) atomicAdd(&outdeg[s], 1u);
-        else raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE);
         if (k >= n) raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE);
     }
     __syncthreads();
@@ -125,7 +122,9 @@ template <int BLOCK, int ITEMS, bool BALLOT = false>
 __global__ void __launch_bounds__(BLOCK) k_csr_pass(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t m, int p, const uint32_t *__restrict__ dstart,
-    uint64_t *status_lb, uint32_t *counters, uint32_t *status, int digit, int base_shift)
+    uint64_t *status_lb, uint32_t *counters, uint32_t *status, int digit, int base_shift,
+    uint32_t *outdeg = nullptr, uint32_t n = 0, const uint32_t *outdeg_in = nullptr,
+    float *val_out = nullptr, uint32_t *ends = nullptr)
 {
     constexpr int TILE = BLOCK * ITEMS;
     constexpr int WARPS = BLOCK / 32;
@@ -159,6 +158,18 @@ __global__ void __launch_bounds__(BLOCK) k_csr_pass(
         } else {
             key[k] = 0xFFFFFFFFu;
             val[k] = 0;
+        }
+    }
+    if (outdeg != nullptr) {
+        // the first pass of the CSR build also counts outdeg(u) over the
+        // values (the sources): fire-and-forget L2 reductions beside the ranking
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            const int64_t i = t0 + warp * WARP_ITEMS + k * 32 + lane;
+            if (i < m) {
+                if (val[k] < n) atomicAdd(&outdeg[val[k]], 1u);
+                else raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE);
+            }
         }
     }
     const uint32_t lt = (1u << lane) - 1u;
@@ -271,10 +282,33 @@ __global__ void __launch_bounds__(BLOCK) k_csr_pass(
         const int j = k * BLOCK + threadIdx.x;
         if (j < valid_n) {
             const uint32_t kk = s_keys[j];
+            const uint32_t vv = s_vals[j];
             const uint32_t dd = (kk >> shift) & 255u;
             const int64_t g = (int64_t)s_base[dd] + (j - (int64_t)s_tpre[dd]);
-            __stcs(kout + g, kk);
-            __stcs(vout + g, s_vals[j]);
+            __stcs(vout + g, vv);
+            if (ends == nullptr) {
+                __stcs(kout + g, kk);
+                continue;
+            }
+            // the last pass of the CSR build: the sorted keys are not kept;
+            // instead val = fp32(1 / outdeg(col)) and the row ends.  Inside
+            // the tile's run of digit dd the keys are sorted, so a key whose
+            // successor in the run differs ends here; a key at the end of the
+            // run may continue in a later tile, so it offers its end by max.
+            const uint32_t dg = vv < n ? __ldg(outdeg_in + vv) : 0u;
+            float r;
+            if (dg == 0) r = 0.0f;
+            else if (dg < (1u << 24)) r = __frcp_rn((float)dg);      // exact operand, IEEE rounding
+            else r = (float)(1.0 / (double)dg);
+            __stcs(val_out + g, r);
+            if (kk < n) {
+                const int run_end = dd < 255u ? (int)s_tpre[dd + 1] : (int)valid_n;
+                if (j + 1 < run_end) {
+                    if (s_keys[j + 1] != kk) ends[kk] = (uint32_t)(g + 1);
+                } else {
+                    atomicMax(&ends[kk], (uint32_t)(g + 1));
+                }
+            }
         }
     }
 }
@@ -697,6 +731,7 @@ extern "C" boba_status_t boba_coo_to_csr(const int32_t *src, const int32_t *dst,
     uint32_t *kA = reinterpret_cast<uint32_t *>(b + L.kA), *vA = reinterpret_cast<uint32_t *>(b + L.vA);
     uint32_t *kB = reinterpret_cast<uint32_t *>(b + L.kB), *vB = reinterpret_cast<uint32_t *>(b + L.vB);
     uint32_t *outdeg = reinterpret_cast<uint32_t *>(b + L.outdeg);
+    uint32_t *ends = reinterpret_cast<uint32_t *>(b + L.ends);
     uint32_t *hist = reinterpret_cast<uint32_t *>(b + L.hist);
     uint32_t *dstart = reinterpret_cast<uint32_t *>(b + L.dstart);
     uint64_t *lb = reinterpret_cast<uint64_t *>(b + L.status);
@@ -712,8 +747,7 @@ extern "C" boba_status_t boba_coo_to_csr(const int32_t *src, const int32_t *dst,
     {
         const int g = persistent_grid((const void *)k_csr_hist, 256, cdiv(m, 256));
         BOBA_TIMED("csr.hist", stream,
-                   k_csr_hist<<<g, 256, 0, stream>>>(src, dst, m, nn, L.passes, outdeg, hist,
-                                                     dev->status));
+                   k_csr_hist<<<g, 256, 0, stream>>>(dst, m, nn, L.passes, hist, dev->status));
     }
     BOBA_TIMED("csr.digits", stream,
                k_csr_digits<<<1, 256, 0, stream>>>(hist, dstart, L.passes));
@@ -723,23 +757,34 @@ extern "C" boba_status_t boba_coo_to_csr(const int32_t *src, const int32_t *dst,
         const bool last = p == L.passes - 1;
         uint32_t *ko = (p & 1) ? kB : kA;
         uint32_t *vo = last ? reinterpret_cast<uint32_t *>(col_out) : ((p & 1) ? vB : vA);
+        // pass 0 counts outdeg; with two or more passes the last one also
+        // writes val and the row ends (outdeg is complete by then)
+        uint32_t *od = p == 0 ? outdeg : nullptr;
+        const bool fuse = last && L.passes > 1;
+        uint32_t *ends_p = fuse ? ends : nullptr;
+        float *val_p = fuse ? val_out : nullptr;
+        const uint32_t *od_in = fuse ? outdeg : nullptr;
         if (tuned_variant(kTuneCsr, m) == 1)
             BOBA_TIMED("csr.pass", stream,
                        k_csr_pass<kPassBlock, kPassItems, true><<<(unsigned)L.tiles, kPassBlock, 0,
                                                                  stream>>>(
-                           kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status, p, 0));
+                           kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status, p, 0, od, nn,
+                           od_in, val_p, ends_p));
         else
             BOBA_TIMED("csr.pass", stream,
                        k_csr_pass<kPassBlock, kPassItems><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
-                           kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status, p, 0));
+                           kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status, p, 0, od, nn,
+                           od_in, val_p, ends_p));
         kin = ko;
         vin = vo;
     }
     {
-        uint32_t *ends = reinterpret_cast<uint32_t *>(b + L.ends);
-        const int g = persistent_grid((const void *)k_csr_ends, 256, cdiv(m, 256));
-        BOBA_TIMED("csr.finish", stream,
-                   k_csr_ends<<<g, 256, 0, stream>>>(kin, col_out, m, nn, outdeg, ends, val_out));
+        if (L.passes == 1) {
+            const int g = persistent_grid((const void *)k_csr_ends, 256, cdiv(m, 256));
+            BOBA_TIMED("csr.finish", stream,
+                       k_csr_ends<<<g, 256, 0, stream>>>(kin, col_out, m, nn, outdeg, ends,
+                                                         val_out));
+        }
         BOBA_TIMED("csr.finish", stream,
                    k_csr_rowptr<<<(unsigned)L.row_tiles, 256, 0, stream>>>(
                        ends, n, row_ptr, reinterpret_cast<uint64_t *>(b + L.rstat), ctr,

@@ -61,13 +61,23 @@ bool pr_layout(int64_t n, int64_t nnz, PrLayout &L)
 }
 
 // has_out bit u = 1 iff u is a column of some entry, i.e. u has an out-edge.
-// A word is read before the atomic so repeated columns cost a load only.
-__global__ void __launch_bounds__(256) k_pr_mark(const int32_t *__restrict__ col, int64_t nnz,
-                                                 int64_t n, uint32_t *has_out, PrState *st,
-                                                 uint32_t *status)
+// Columns below kHubCols (after BOBA, the vertices met first: the busiest
+// columns) are collected in a per-block shared bitmap and merged once per
+// block, so the hot words are not hammered in L2; the others are set with a
+// global atomic after a check that the bit is still clear.
+constexpr int kHubCols = 65536;
+constexpr int kMarkBlock = 512;
+
+__global__ void __launch_bounds__(kMarkBlock) k_pr_mark(const int32_t *__restrict__ col,
+                                                        int64_t nnz, int64_t n, uint32_t *has_out,
+                                                        PrState *st, uint32_t *status)
 {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz; j += stride) {
+    __shared__ uint32_t s_bits[kHubCols / 32];
+    const int hub_words = (int)((n < kHubCols ? n : kHubCols) + 31) / 32;
+    for (int i = threadIdx.x; i < hub_words; i += kMarkBlock) s_bits[i] = 0;
+    __syncthreads();
+    const int64_t stride = (int64_t)gridDim.x * kMarkBlock;
+    for (int64_t j = (int64_t)blockIdx.x * kMarkBlock + threadIdx.x; j < nnz; j += stride) {
         const int32_t u = __ldcs(col + j);
         if (u < 0 || (int64_t)u >= n) {
             raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE);
@@ -75,7 +85,16 @@ __global__ void __launch_bounds__(256) k_pr_mark(const int32_t *__restrict__ col
             continue;
         }
         const uint32_t bit = 1u << (u & 31);
-        if ((__ldcg(has_out + (u >> 5)) & bit) == 0) atomicOr(has_out + (u >> 5), bit);
+        if (u < kHubCols) {
+            if ((s_bits[u >> 5] & bit) == 0) atomicOr(&s_bits[u >> 5], bit);
+        } else if ((__ldcg(has_out + (u >> 5)) & bit) == 0) {
+            atomicOr(has_out + (u >> 5), bit);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < hub_words; i += kMarkBlock) {
+        const uint32_t w = s_bits[i];
+        if (w != 0 && (__ldcg(has_out + i) & w) != w) atomicOr(has_out + i, w);
     }
 }
 
@@ -109,7 +128,9 @@ __global__ void __launch_bounds__(kPrBlock) k_pr_update(
     const float df = (float)d;
     const float base = INIT ? 0.0f : (float)st->base;
     const float inv_n = (float)(1.0 / (double)n);
-    double change = 0.0, dangling = 0.0;
+    // a thread's 16 terms are summed in fp32 (relative error below 1e-6), the
+    // block and tile sums in fp64: few fp64 operations, which are slow here
+    float change = 0.0f, dangling = 0.0f;
     const int64_t v0 = (int64_t)blockIdx.x * kPrTile;
     for (int k = threadIdx.x; k < kPrTile; k += kPrBlock) {
         const int64_t v = v0 + k;
@@ -120,13 +141,13 @@ __global__ void __launch_bounds__(kPrBlock) k_pr_update(
         } else {
             const float old = pr[v];
             nv = fmaf(df, __ldcs(y + v), base);
-            change += fabs((double)nv - (double)old);
+            change += fabsf(nv - old);
         }
         pr[v] = nv;
-        if (((__ldg(has_out + (v >> 5)) >> (v & 31)) & 1u) == 0) dangling += (double)nv;
+        if (((__ldg(has_out + (v >> 5)) >> (v & 31)) & 1u) == 0) dangling += nv;
     }
-    const double c = block_sum_fixed(change, s_warp);
-    const double g = block_sum_fixed(dangling, s_warp);
+    const double c = block_sum_fixed((double)change, s_warp);
+    const double g = block_sum_fixed((double)dangling, s_warp);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = make_double2(c, g);
         __threadfence();
@@ -206,9 +227,9 @@ extern "C" boba_status_t boba_pagerank(const int64_t *row_ptr, const int32_t *co
     BOBA_CUDA_TRY(cudaMemsetAsync(has_out, 0, (size_t)(cdiv(n, 32) + 1) * 4, s));
     BOBA_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(PrState), s));
     if (nnz > 0) {
-        const int g = persistent_grid((const void *)k_pr_mark, 256, cdiv(nnz, 256));
+        const int g = persistent_grid((const void *)k_pr_mark, kMarkBlock, cdiv(nnz, kMarkBlock));
         BOBA_TIMED("pagerank.mark", s,
-                   k_pr_mark<<<g, 256, 0, s>>>(col, nnz, n, has_out, st, dev->status));
+                   k_pr_mark<<<g, kMarkBlock, 0, s>>>(col, nnz, n, has_out, st, dev->status));
     }
     const unsigned tiles = (unsigned)L.pr_tiles;
     BOBA_TIMED("pagerank.update", s,
@@ -216,7 +237,7 @@ extern "C" boba_status_t boba_pagerank(const int64_t *row_ptr, const int32_t *co
                                                             max_iters, st, part, iters_out,
                                                             residual_out));
     int variant = tuned_variant(kTuneSpmv, nnz);
-    if (variant < 5 || variant > 8) variant = 5;
+    if (variant < 5 || variant > 10) variant = 5;
     if (max_iters > 0)
         merge_path_partition(row_ptr, n, nnz, merge_path_items(variant), mp_part, s);
     for (int64_t t = 0; t < max_iters; ++t) {

@@ -209,26 +209,38 @@ struct KV {
     float v;
 };
 
+// The shared arrays of one merge-path tile, padded one word per 32 (a thread
+// walks MI consecutive items, so without the padding the lanes of a warp would
+// hit the same few banks): the row ends of the tile's rows, then the products
+// of its nonzeros, in one buffer -- rows and nonzeros together are the tile's
+// MB * MI path items, so one tile's worth of words holds both.  Half the
+// shared memory of two separate arrays leaves that much more L1 for the x
+// gathers.  And the warp carries.
 template <int MB, int MI>
-__global__ void __launch_bounds__(MB) k_mp_spmv(
-    const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
-    const float *__restrict__ val, const float *__restrict__ x, float *__restrict__ y, int64_t n,
-    int64_t nnz, const int2 *__restrict__ part, int32_t *__restrict__ carry_row,
-    float *__restrict__ carry_val, const uint32_t *skip)
+struct MpSmem {
+    static constexpr int kWords = MB * MI + MB * MI / 32 + 4;
+    int32_t s_buf[kWords];
+    KV s_warp[MB / 32];
+};
+
+// One tile of the merge path: the tile's rows and nonzeros split evenly over
+// the MB threads (MI path items each).
+template <int MB, int MI>
+__device__ __forceinline__ void mp_tile(
+    int64_t tile, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+    const float *__restrict__ val, const float *__restrict__ x, float *__restrict__ y,
+    const int2 *__restrict__ part, int32_t *__restrict__ carry_row, float *__restrict__ carry_val,
+    MpSmem<MB, MI> &sm)
 {
-    if (skip != nullptr && *skip != 0) return;       // an iterative caller has converged
-    constexpr int kMpBlock = MB, kMpItems = MI, kMpTile = MB * MI;
-    // one pad word per 32: a thread walks MI consecutive items, so without the
-    // padding the lanes of a warp would hit the same few banks
-    constexpr int kPadded = kMpTile + kMpTile / 32 + 2;
-    __shared__ int32_t s_end[kPadded];         // row ends of the tile's rows, relative to y0
-    __shared__ float s_prod[kPadded];          // products of the tile's nonzeros
-    __shared__ KV s_warp[kMpBlock / 32];
+    constexpr int kMpBlock = MB, kMpItems = MI;
     auto P = [](int j) { return j + (j >> 5); };
-    const int64_t tile = blockIdx.x;
     const int2 p0 = part[tile], p1 = part[tile + 1];
     const int x0 = p0.x, y0 = p0.y;
     const int nrows = p1.x - p0.x, nnzt = p1.y - p0.y;
+    // row ends at P(0 .. nrows) (the last one a sentinel), products after them
+    int32_t *s_end = sm.s_buf;
+    float *s_prod = reinterpret_cast<float *>(sm.s_buf + P(nrows) + 1);
+    KV *s_warp = sm.s_warp;
     for (int i = threadIdx.x; i < nrows; i += kMpBlock)
         s_end[P(i)] = (int32_t)(__ldg(row_ptr + x0 + 1 + i) - y0);
     if (threadIdx.x == 0) s_end[P(nrows)] = 0x7FFFFFFF;   // sentinel: no row end beyond
@@ -310,6 +322,21 @@ __global__ void __launch_bounds__(MB) k_mp_spmv(
     }
 }
 
+
+// CARVE only makes separate instances, so that a shared-memory carve-out set
+// for one variant does not apply to the others.
+template <int MB, int MI, int CARVE = 0>
+__global__ void __launch_bounds__(MB) k_mp_spmv(
+    const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
+    const float *__restrict__ val, const float *__restrict__ x, float *__restrict__ y, int64_t n,
+    int64_t nnz, const int2 *__restrict__ part, int32_t *__restrict__ carry_row,
+    float *__restrict__ carry_val, const uint32_t *skip)
+{
+    if (skip != nullptr && *skip != 0) return;       // an iterative caller has converged
+    __shared__ MpSmem<MB, MI> sm;
+    mp_tile<MB, MI>(blockIdx.x, row_ptr, col, val, x, y, part, carry_row, carry_val, sm);
+}
+
 // y[r] += the carries of the tiles that ended inside row r, in tile order.
 __global__ void __launch_bounds__(256) k_mp_fixup(const int32_t *__restrict__ carry_row,
                                                   const float *__restrict__ carry_val,
@@ -348,6 +375,25 @@ int merge_path_items(int variant)
     return variant == 6 ? 3072 : variant == 7 ? 4096 : 2048;
 }
 
+namespace {
+
+// The 256x8 merge path with the shared-memory carve-out capped at `kb` KB per
+// SM: fewer resident blocks, more L1 for the x gathers (whose L1 hits are the
+// high-degree columns that BOBA puts first).
+template <int CARVE>
+void launch_carved(int kb, const int64_t *row_ptr, const int32_t *col, const float *val,
+                   const float *x, float *y, int64_t n, int64_t nnz, const int2 *part,
+                   int32_t *crow, float *cval, const uint32_t *skip, int64_t tiles,
+                   cudaStream_t stream)
+{
+    cudaFuncSetAttribute((const void *)k_mp_spmv<256, 8, CARVE>,
+                         cudaFuncAttributePreferredSharedMemoryCarveout, kb * 100 / 228);
+    BOBA_TIMED("spmv", stream, k_mp_spmv<256, 8, CARVE><<<(unsigned)tiles, 256, 0, stream>>>(
+                                   row_ptr, col, val, x, y, n, nnz, part, crow, cval, skip));
+}
+
+}  // namespace
+
 void merge_path_partition(const int64_t *row_ptr, int64_t n, int64_t nnz, int items, int2 *part,
                           cudaStream_t stream)
 {
@@ -362,7 +408,11 @@ void merge_path_multiply(int variant, const int64_t *row_ptr, const int32_t *col
                          int32_t *crow, float *cval, const uint32_t *skip, cudaStream_t stream)
 {
     const int64_t tiles = cdiv(n + nnz, merge_path_items(variant));
-    if (variant == 6)
+    if (variant == 9)
+        launch_carved<1>(64, row_ptr, col, val, x, y, n, nnz, part, crow, cval, skip, tiles, stream);
+    else if (variant == 10)
+        launch_carved<2>(32, row_ptr, col, val, x, y, n, nnz, part, crow, cval, skip, tiles, stream);
+    else if (variant == 6)
         BOBA_TIMED("spmv", stream, k_mp_spmv<256, 12><<<(unsigned)tiles, 256, 0, stream>>>(
                                        row_ptr, col, val, x, y, n, nnz, part, crow, cval, skip));
     else if (variant == 7)
@@ -414,8 +464,9 @@ extern "C" boba_status_t boba_spmv_csr(const int64_t *row_ptr, const int32_t *co
     const uint32_t cap = (uint32_t)L.cap;
 
     const int tv = tuned_variant(kTuneSpmv, nnz);
-    // 0 auto, 1..4: LPR 4, 8, 16, 32; 5..8: merge path (block x items) 256x8, 256x12, 512x8, 128x16
-    if (tv >= 5 && tv <= 8) {
+    // 0 auto, 1..4: LPR 4, 8, 16, 32; 5..8: merge path (block x items) 256x8, 256x12, 512x8,
+    // 128x16; 9, 10: merge path 256x8 with the shared-memory carve-out capped at 64, 32 KB
+    if (tv >= 5 && tv <= 10) {
         int2 *part = reinterpret_cast<int2 *>(b + L.mp_part);
         int32_t *crow = reinterpret_cast<int32_t *>(b + L.mp_crow);
         float *cval = reinterpret_cast<float *>(b + L.mp_cval);
