@@ -54,7 +54,7 @@ int tuned_variant(int kernel, int64_t size);
 int size_class(int64_t size);
 
 // Merge-path SpMV (spmv.cu), shared with the iterative callers.  `variant` is a
-// tuned SpMV variant 5..10 (anything else means 5): it fixes the block shape,
+// tuned SpMV variant 5..13 (anything else means 5): it fixes the block shape,
 // the path items per tile and the shared-memory carve-out.  The partition depends on row_ptr only, so an
 // iterative caller computes it once.  A non-null `skip` pointing at a nonzero
 // word makes the multiply's kernels return at once.

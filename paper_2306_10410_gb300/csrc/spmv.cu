@@ -370,25 +370,45 @@ void launch_rows(const int64_t *row_ptr, const int32_t *col, const float *val, c
 
 }  // namespace
 
+// Merge-path shapes of the tuned SpMV variants 5 .. 13: threads per block,
+// path items per thread, and the cap on the shared-memory carve-out in KB
+// (0: the default, which maximises resident blocks).  A smaller carve-out
+// trades resident warps for L1, which holds the hot x entries.
+struct MpShape {
+    int block, items, carve_kb;
+};
+constexpr MpShape kMpShapes[] = {
+    {256, 8, 0}, {256, 12, 0}, {512, 8, 0}, {128, 16, 0},          // 5 .. 8
+    {256, 8, 64}, {256, 8, 32}, {256, 12, 64}, {512, 8, 64},       // 9 .. 12
+    {256, 16, 64},                                                 // 13
+};
+constexpr int kMpFirst = 5, kMpLast = 13;
+
+MpShape mp_shape(int variant)
+{
+    if (variant < kMpFirst || variant > kMpLast) variant = kMpFirst;
+    return kMpShapes[variant - kMpFirst];
+}
+
 int merge_path_items(int variant)
 {
-    return variant == 6 ? 3072 : variant == 7 ? 4096 : 2048;
+    const MpShape sh = mp_shape(variant);
+    return sh.block * sh.items;
 }
 
 namespace {
 
-// The 256x8 merge path with the shared-memory carve-out capped at `kb` KB per
-// SM: fewer resident blocks, more L1 for the x gathers (whose L1 hits are the
-// high-degree columns that BOBA puts first).
-template <int CARVE>
-void launch_carved(int kb, const int64_t *row_ptr, const int32_t *col, const float *val,
-                   const float *x, float *y, int64_t n, int64_t nnz, const int2 *part,
-                   int32_t *crow, float *cval, const uint32_t *skip, int64_t tiles,
-                   cudaStream_t stream)
+// One launch of k_mp_spmv<MB, MI, CARVE>; with a carve-out cap the attribute
+// is set on that instance only.
+template <int MB, int MI, int CARVE>
+void launch_mp(int carve_kb, const int64_t *row_ptr, const int32_t *col, const float *val,
+               const float *x, float *y, int64_t n, int64_t nnz, const int2 *part, int32_t *crow,
+               float *cval, const uint32_t *skip, int64_t tiles, cudaStream_t stream)
 {
-    cudaFuncSetAttribute((const void *)k_mp_spmv<256, 8, CARVE>,
-                         cudaFuncAttributePreferredSharedMemoryCarveout, kb * 100 / 228);
-    BOBA_TIMED("spmv", stream, k_mp_spmv<256, 8, CARVE><<<(unsigned)tiles, 256, 0, stream>>>(
+    if (carve_kb > 0)
+        cudaFuncSetAttribute((const void *)k_mp_spmv<MB, MI, CARVE>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, carve_kb * 100 / 228);
+    BOBA_TIMED("spmv", stream, k_mp_spmv<MB, MI, CARVE><<<(unsigned)tiles, MB, 0, stream>>>(
                                    row_ptr, col, val, x, y, n, nnz, part, crow, cval, skip));
 }
 
@@ -407,23 +427,26 @@ void merge_path_multiply(int variant, const int64_t *row_ptr, const int32_t *col
                          const float *x, float *y, int64_t n, int64_t nnz, const int2 *part,
                          int32_t *crow, float *cval, const uint32_t *skip, cudaStream_t stream)
 {
+    if (variant < kMpFirst || variant > kMpLast) variant = kMpFirst;
     const int64_t tiles = cdiv(n + nnz, merge_path_items(variant));
-    if (variant == 9)
-        launch_carved<1>(64, row_ptr, col, val, x, y, n, nnz, part, crow, cval, skip, tiles, stream);
-    else if (variant == 10)
-        launch_carved<2>(32, row_ptr, col, val, x, y, n, nnz, part, crow, cval, skip, tiles, stream);
-    else if (variant == 6)
-        BOBA_TIMED("spmv", stream, k_mp_spmv<256, 12><<<(unsigned)tiles, 256, 0, stream>>>(
-                                       row_ptr, col, val, x, y, n, nnz, part, crow, cval, skip));
-    else if (variant == 7)
-        BOBA_TIMED("spmv", stream, k_mp_spmv<512, 8><<<(unsigned)tiles, 512, 0, stream>>>(
-                                       row_ptr, col, val, x, y, n, nnz, part, crow, cval, skip));
-    else if (variant == 8)
-        BOBA_TIMED("spmv", stream, k_mp_spmv<128, 16><<<(unsigned)tiles, 128, 0, stream>>>(
-                                       row_ptr, col, val, x, y, n, nnz, part, crow, cval, skip));
-    else
-        BOBA_TIMED("spmv", stream, k_mp_spmv<256, 8><<<(unsigned)tiles, 256, 0, stream>>>(
-                                       row_ptr, col, val, x, y, n, nnz, part, crow, cval, skip));
+    const int kb = mp_shape(variant).carve_kb;
+#define BOBA_MP(V, MB, MI, C)                                                                  \
+    case V:                                                                                    \
+        launch_mp<MB, MI, C>(kb, row_ptr, col, val, x, y, n, nnz, part, crow, cval, skip, tiles, \
+                             stream);                                                          \
+        break;
+    switch (variant) {
+        BOBA_MP(5, 256, 8, 0)
+        BOBA_MP(6, 256, 12, 0)
+        BOBA_MP(7, 512, 8, 0)
+        BOBA_MP(8, 128, 16, 0)
+        BOBA_MP(9, 256, 8, 1)
+        BOBA_MP(10, 256, 8, 2)
+        BOBA_MP(11, 256, 12, 1)
+        BOBA_MP(12, 512, 8, 1)
+        BOBA_MP(13, 256, 16, 1)
+    }
+#undef BOBA_MP
     BOBA_TIMED("spmv.fixup", stream,
                k_mp_fixup<<<(unsigned)cdiv(tiles, 256), 256, 0, stream>>>(crow, cval, tiles, n, y,
                                                                            skip));
@@ -464,9 +487,8 @@ extern "C" boba_status_t boba_spmv_csr(const int64_t *row_ptr, const int32_t *co
     const uint32_t cap = (uint32_t)L.cap;
 
     const int tv = tuned_variant(kTuneSpmv, nnz);
-    // 0 auto, 1..4: LPR 4, 8, 16, 32; 5..8: merge path (block x items) 256x8, 256x12, 512x8,
-    // 128x16; 9, 10: merge path 256x8 with the shared-memory carve-out capped at 64, 32 KB
-    if (tv >= 5 && tv <= 10) {
+    // 0 auto, 1..4: LPR 4, 8, 16, 32; 5..13: merge path, shapes in kMpShapes
+    if (tv >= kMpFirst && tv <= kMpLast) {
         int2 *part = reinterpret_cast<int2 *>(b + L.mp_part);
         int32_t *crow = reinterpret_cast<int32_t *>(b + L.mp_crow);
         float *cval = reinterpret_cast<float *>(b + L.mp_cval);

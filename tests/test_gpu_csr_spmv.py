@@ -149,7 +149,7 @@ def test_full_size_rmat24_csr_spmv(boba):
     check_spmv(boba, (rp, col, val), (orp, ocol, oval), synth.uniform_f32(w.n, seed=w.seed))
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10])
+@pytest.mark.parametrize("variant", list(range(14)))
 @pytest.mark.parametrize("case", ["rmat14", "hubs", "empty_rows", "one_row", "no_edges"])
 def test_spmv_variants(boba, variant, case):
     """Every SpMV variant (lanes per row 4..32, merge path) within the fp32 bound,
