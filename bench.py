@@ -597,11 +597,11 @@ def run_e2e(args, boba, torch, dev, stream, src_h, dst_h, m, n, world):
         ev[1].record(streams[0])
         torch.cuda.synchronize(dev)
         lat.append(ev[0].elapsed_time(ev[1]))
-    # K steps back to back on alternating streams; three rounds, the median
+    # K steps back to back on alternating streams; five rounds, the median
     # round is reported (the host link is shared with the machine's other work)
     steps = max(2, min(args.steps, 10))
     rounds = []
-    for _ in range(3):
+    for _ in range(5):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(streams[0])
         streams[1].wait_event(ev0)

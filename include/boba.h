@@ -46,14 +46,14 @@ typedef enum boba_status {
 } boba_status_t;
 
 /* ------------------------------------------------------------------------
- * Reordering (Sec. 4.3 Alg. 1 and Sec. 4.5 Alg. 2 with an AtomicMin update)
+ * Reordering (Sec. 4.3 Alg. 1 and Sec. 4.4 Alg. 2 with an AtomicMin update)
  * ------------------------------------------------------------------------ */
 
 /*
  * boba_reorder -- the BOBA ordering of one COO graph and the relabelled edges.
  *
  * Computes, for every vertex v, key(v) = the lowest position at which v occurs
- * in I ++ J (Alg. 2 with AtomicMin, Sec. 4.5, which the paper notes recovers
+ * in I ++ J (Alg. 2 with AtomicMin, Sec. 4.4, which the paper notes recovers
  * the first-occurrence order of Alg. 1, Sec. 4.3), orders the vertices that
  * occur by increasing key, and appends the vertices that occur in no edge in
  * ascending original ID.  Then rewrites each edge through the new labels
@@ -162,7 +162,7 @@ size_t boba_reorder_host_workspace_bytes(int64_t m, int64_t n);
  *   variant 0  first occurrence in I ++ J (the default; same as boba_reorder_ex)
  *   variant 1  first occurrence in the interleaved list I(0) J(0) I(1) J(1) ...,
  *              the flattening drawn in Fig. 1 (deterministic, bit-exact)
- *   variant 2  Alg. 2 exactly as printed (Sec. 4.5): a plain, racy store instead
+ *   variant 2  Alg. 2 exactly as printed (Sec. 4.4): a plain, racy store instead
  *              of AtomicMin, which the paper found as good in practice.  The
  *              chosen key of a vertex is one of its positions but not always the
  *              lowest, so the result may differ from run to run; it is always a
@@ -179,7 +179,7 @@ boba_status_t boba_reorder_variant(const int32_t *src, const int32_t *dst, int64
 
 /*
  * boba_first_keys -- lowers key[v] to the lowest position of v among the
- * given edges (Alg. 2 with AtomicMin, Sec. 4.5), where local edge e holds
+ * given edges (Alg. 2 with AtomicMin, Sec. 4.4), where local edge e holds
  * positions pos_src + e (its source) and pos_dst + e (its destination) of the
  * global stream I ++ J.  For a shard [e0, e1) of a graph with m edges, pass
  * the shard's arrays with pos_src = e0, pos_dst = m + e0.

@@ -9,7 +9,7 @@ The arithmetic lives in ``boba_oracle.c`` (single-threaded C, compiled here with
 gcc); this module only marshals numpy arrays.  Every function cites the passage
 of the paper it follows:
 
-* :func:`first_keys`   -- Algorithm 2's key r with an AtomicMin update (Sec. 4.5)
+* :func:`first_keys`   -- Algorithm 2's key r with an AtomicMin update (Sec. 4.4)
 * :func:`boba_perm`    -- Algorithm 1, Sequential BOBA (Sec. 4.3), plus the
                           isolated-vertex tail (ascending original ID)
 * :func:`boba_perm_interleaved` -- the interleaved flattening drawn in Fig. 1

@@ -31,7 +31,7 @@ static int check_ids(const int32_t *a, int64_t m, int64_t n)
 }
 
 /*
- * First-occurrence keys, the r of Algorithm 2 (Sec. 4.5) when its update is an
+ * First-occurrence keys, the r of Algorithm 2 (Sec. 4.4) when its update is an
  * AtomicMin: key[v] = min{ i in [0, 2m) : (I ++ J)(i) = v }, and the sentinel
  * 0xFFFFFFFF (the paper's "infinity") for a vertex in no edge.
  * Written as the definition: one ascending scan that keeps the first hit.

@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(256) k_csr_digits(const uint32_t *__restrict__
 // One stable LSD pass over digit p (bits 8p .. 8p+7).  BLOCK threads hold
 // ITEMS items each; the first 256 threads also own one digit each for the
 // cross-tile look-back.
-template <int BLOCK, int ITEMS, bool BALLOT = false>
-__global__ void __launch_bounds__(BLOCK) k_csr_pass(
+template <int BLOCK, int ITEMS, bool BALLOT = false, int MINB = 1>
+__global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t m, int p, const uint32_t *__restrict__ dstart,
     uint64_t *status_lb, uint32_t *counters, uint32_t *status, int digit, int base_shift,
@@ -764,10 +764,19 @@ extern "C" boba_status_t boba_coo_to_csr(const int32_t *src, const int32_t *dst,
         uint32_t *ends_p = fuse ? ends : nullptr;
         float *val_p = fuse ? val_out : nullptr;
         const uint32_t *od_in = fuse ? outdeg : nullptr;
-        if (tuned_variant(kTuneCsr, m) == 1)
+        const int tv = tuned_variant(kTuneCsr, m);
+        // 0: match ranking; 1: ballot ranking; 2: ballot ranking with registers
+        // capped for three resident blocks per SM
+        if (tv == 1)
             BOBA_TIMED("csr.pass", stream,
                        k_csr_pass<kPassBlock, kPassItems, true><<<(unsigned)L.tiles, kPassBlock, 0,
                                                                  stream>>>(
+                           kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status, p, 0, od, nn,
+                           od_in, val_p, ends_p));
+        else if (tv == 2)
+            BOBA_TIMED("csr.pass", stream,
+                       k_csr_pass<kPassBlock, kPassItems, true, 3><<<(unsigned)L.tiles, kPassBlock,
+                                                                    0, stream>>>(
                            kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status, p, 0, od, nn,
                            od_in, val_p, ends_p));
         else

@@ -1,4 +1,4 @@
-// BOBA reordering of one COO graph (arXiv 2306.10410, Sec. 4.3 and Sec. 4.5).
+// BOBA reordering of one COO graph (arXiv 2306.10410, Sec. 4.3 and Sec. 4.4).
 //
 // Pipeline (all on one stream, no host synchronisation):
 //   k_init      key[v] = SENT; clear the rank bitmap and scan state
@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256) k_init(uint32_t *__restrict__ key, int64_
 
 // ---------------------------------------------------------------------------
 // k_first: for every position i of I ++ J, key[(I++J)[i]] = min(key, i).
-// Alg. 2 (Sec. 4.5) with its update made an AtomicMin, which the paper notes
+// Alg. 2 (Sec. 4.4) with its update made an AtomicMin, which the paper notes
 // yields exactly the lowest position (the order of Alg. 1).
 // Work order: the grid sweeps the stream from position 0 upwards in chunks of
 // kFirstBlock*kFirstUnroll int4 loads per block, so by the time a position is
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kFirstBlock) k_first_at(const int32_t *__restr
     first_body<VEC, kFirstBlock, kFirstUnroll>(src, dst, m, n, key, status, pos_src, pos_dst);
 }
 
-// Alg. 2 exactly as printed (Sec. 4.5): the same sweep with a plain store in
+// Alg. 2 exactly as printed (Sec. 4.4): the same sweep with a plain store in
 // place of the AtomicMin.  Faster under contention, not deterministic.
 template <bool VEC>
 __global__ void __launch_bounds__(kFirstBlock) k_first_racy(const int32_t *__restrict__ src,

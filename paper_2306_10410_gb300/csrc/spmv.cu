@@ -13,6 +13,10 @@
 // Every summation order depends only on the row's own entries (and on LPR, a
 // function of nnz / n_rows), so the result is the same on every run, and rows of
 // equal content give equal bits whatever their index.
+//
+//   k_mp_partition / k_mp_spmv / k_mp_fixup   the merge-path SpMV (below),
+//                  the tuned choice for skewed graphs; its shapes differ in
+//                  block size, items per thread and shared-memory carve-out.
 #include "common.cuh"
 #include "host.hpp"
 
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(256) k_spmv_gather(const uint32_t *long_count,
 // ---------------------------------------------------------------------------
 // Merge-path SpMV (Merrill and Garland, "Merge-based parallel sparse matrix-
 // vector multiplication", SC 2016), the load balancing of the paper's
-// evaluation (Sec. 3.4): the path of n_rows row ends and nnz nonzeros is cut
+// evaluation (Sec. 3.3 and 5.1): the path of n_rows row ends and nnz nonzeros is cut
 // into tiles of kMpTile items, so every block gets the same work whatever the
 // row lengths.  Sums run in path order within a thread, then a segmented scan
 // over the threads of a tile, then (for rows crossing tiles) the tiles'

@@ -91,7 +91,7 @@ def test_csr_ranking_variants_bit_identical(boba):
     I, J = synth.rmat(17, 800_001, seed=35)
     n = 1 << 17
     orp, ocol, oval = oracle.coo_to_csr(I, J, n)
-    for v in (0, 1):
+    for v in (0, 1, 2):
         boba.load().boba_tune_set(boba.TUNE_CSR, len(I), v)
         rp, col, val = boba.coo_to_csr(torch.from_numpy(I).cuda(), torch.from_numpy(J).cuda(), n)
         boba.stream_status()
@@ -99,5 +99,5 @@ def test_csr_ranking_variants_bit_identical(boba):
         np.testing.assert_array_equal(col.cpu().numpy(), ocol)
         np.testing.assert_array_equal(val.cpu().numpy(), oval)
     ch = boba.tune_csr(torch.from_numpy(I).cuda(), torch.from_numpy(J).cuda(), n, reps=2)
-    assert ch["csr"] in (0, 1)
+    assert ch["csr"] in (0, 1, 2)
     boba.tune_reset()

@@ -64,7 +64,7 @@ def test_racy_store_is_valid_and_close(boba):
     assert np.array_equal(p[s], I) and np.array_equal(p[d], J)      # edges consistent
     app = len(np.unique(np.concatenate([I, J])))
     assert np.all(np.diff(p[app:]) > 0)                             # isolated tail ascending
-    # quality: NBR of the racy ordering close to the exact one (Sec. 4.5's claim)
+    # quality: NBR of the racy ordering close to the exact one (Sec. 4.4's claim)
     operm, oso, odo = oracle.reorder(I, J, n)
     v_exact, _ = boba.nbr(*[torch.from_numpy(a).cuda() for a in oracle.coo_to_csr(oso, odo, n)[:2]])
     v_racy, _ = boba.nbr(*[torch.from_numpy(a).cuda() for a in oracle.coo_to_csr(s, d, n)[:2]])
