@@ -532,6 +532,11 @@ def run_batched(args, boba, torch, dev, stream, flush, n_batch=4096, seed=None):
     for _ in range(args.warmup):
         batched(stream)
     t_batched = timed(batched, reps)
+    flush.zero_()
+    with boba.kernel_timing() as kt:                # per-kernel split of one batched call
+        batched(stream)
+        torch.cuda.synchronize(dev)
+    split = {k: round(t, 3) for k, (t, _) in sorted(kt.result.items())}
     per_graph(stream)
     t_pergraph = timed(per_graph, reps)
     boba.stream_status(stream)
@@ -561,6 +566,7 @@ def run_batched(args, boba, torch, dev, stream, flush, n_batch=4096, seed=None):
             "per_graph_ms": round(t_pergraph, 3),
             "per_graph_gedges_s": round(E / (t_pergraph * 1e-3) / 1e9, 3),
             "speedup_batched_vs_per_graph": round(t_pergraph / t_batched, 3),
+            "kernels_ms": split,
             "cuda_graph_ms": t_graph,
             "schedule": {0: "split", 1: "cluster"}.get((tuned or {}).get("batched", 0)),
             "bit_identical": identical}

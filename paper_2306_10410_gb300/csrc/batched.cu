@@ -449,12 +449,24 @@ struct LargeItem {
     uint32_t local;          // chunk / tile index within the graph
 };
 
+// The graph that owns item x.  A block's items only move forward, so thread 0
+// first tries the graph of its previous item (`hint`) and the next few before
+// falling back to a binary search over all large graphs.
 __device__ __forceinline__ void block_find(const BatchArgs &a, const uint32_t *tab, uint32_t x,
-                                           LargeItem &it, LargeItem &s_it)
+                                           LargeItem &it, LargeItem &s_it, uint32_t &hint)
 {
     if (threadIdx.x == 0) {
         const uint32_t L = a.hdr[kHdrLarge];
-        s_it.j = find_graph(tab, L, x);
+        uint32_t j = hint;
+        bool found = false;
+        for (int k = 0; k < 4 && j < L; ++k, ++j) {
+            const uint32_t lo = __ldg(tab + j);
+            if (lo > x) break;
+            if (x < __ldg(tab + j + 1)) { found = true; break; }
+        }
+        if (!found) j = find_graph(tab, L, x);
+        hint = j;
+        s_it.j = j;
         const uint32_t g = a.order[s_it.j];
         s_it.E0 = a.eoff[g];
         s_it.m = a.eoff[g + 1] - s_it.E0;
@@ -485,12 +497,13 @@ __global__ void __launch_bounds__(kLB) k_bl_init(BatchArgs a)
 __global__ void __launch_bounds__(kLB) k_bl_first(BatchArgs a)
 {
     __shared__ LargeItem s_it;
+    uint32_t hint = 0;                     // thread 0: graph of the previous item
     const uint32_t L = a.hdr[kHdrLarge];
     const uint32_t total = a.lg_pc[L];
     constexpr int U = kPosChunk / kLB;
     for (uint32_t c = blockIdx.x; c < total; c += gridDim.x) {
         LargeItem it;
-        block_find(a, a.lg_pc, c, it, s_it);
+        block_find(a, a.lg_pc, c, it, s_it, hint);
         const uint32_t nn = (uint32_t)it.n;
         uint32_t *key = a.kl + (size_t)a.lg_vt[it.j] * kVtxTile;
         const int64_t p0 = (int64_t)it.local * kPosChunk;
@@ -518,11 +531,12 @@ __global__ void __launch_bounds__(kLB) k_bl_first(BatchArgs a)
 __global__ void __launch_bounds__(kLB) k_bl_mark(BatchArgs a)
 {
     __shared__ LargeItem s_it;
+    uint32_t hint = 0;                     // thread 0: graph of the previous item
     const uint32_t L = a.hdr[kHdrLarge];
     const uint32_t total = a.lg_vt[L];
     for (uint32_t c = blockIdx.x; c < total; c += gridDim.x) {
         LargeItem it;
-        block_find(a, a.lg_vt, c, it, s_it);
+        block_find(a, a.lg_vt, c, it, s_it, hint);
         const uint32_t *key = a.kl + (size_t)a.lg_vt[it.j] * kVtxTile;
         uint32_t *bm = a.lbm + (size_t)a.lg_wt[it.j] * kWordTile;
         const int64_t v0 = (int64_t)it.local * kVtxTile + 4 * threadIdx.x;
@@ -537,6 +551,7 @@ __global__ void __launch_bounds__(kLB) k_bl_mark(BatchArgs a)
 __global__ void __launch_bounds__(kLB) k_bl_scan(BatchArgs a)
 {
     __shared__ LargeItem s_it;
+    uint32_t hint = 0;                     // thread 0: graph of the previous item
     __shared__ typename BlockScan<kLB>::Smem sm;
     __shared__ uint32_t s_tile;
     __shared__ uint64_t s_pre;
@@ -549,7 +564,7 @@ __global__ void __launch_bounds__(kLB) k_bl_scan(BatchArgs a)
         __syncthreads();
         if (t >= total) break;
         LargeItem it;
-        block_find(a, a.lg_wt, t, it, s_it);
+        block_find(a, a.lg_wt, t, it, s_it, hint);
         const size_t w0 = (size_t)t * kWordTile + 8 * threadIdx.x;
         const uint4 x0 = __ldcg(reinterpret_cast<const uint4 *>(a.lbm + w0));
         const uint4 x1 = __ldcg(reinterpret_cast<const uint4 *>(a.lbm + w0) + 1);
@@ -571,6 +586,7 @@ __global__ void __launch_bounds__(kLB) k_bl_scan(BatchArgs a)
 __global__ void __launch_bounds__(kLB) k_bl_emit(BatchArgs a)
 {
     __shared__ LargeItem s_it;
+    uint32_t hint = 0;                     // thread 0: graph of the previous item
     __shared__ typename BlockScan<kLB>::Smem sm;
     __shared__ uint32_t s_tile;
     __shared__ uint64_t s_pre;
@@ -583,7 +599,7 @@ __global__ void __launch_bounds__(kLB) k_bl_emit(BatchArgs a)
         __syncthreads();
         if (t >= total) break;
         LargeItem it;
-        block_find(a, a.lg_vt, t, it, s_it);
+        block_find(a, a.lg_vt, t, it, s_it, hint);
         uint32_t *key = a.kl + (size_t)a.lg_vt[it.j] * kVtxTile;
         const size_t wbase = (size_t)a.lg_wt[it.j] * kWordTile;
         const int64_t v0 = (int64_t)it.local * kVtxTile + 4 * threadIdx.x;
@@ -634,12 +650,13 @@ __global__ void __launch_bounds__(kLB) k_bl_emit(BatchArgs a)
 __global__ void __launch_bounds__(kLB) k_bl_relabel(BatchArgs a)
 {
     __shared__ LargeItem s_it;
+    uint32_t hint = 0;                     // thread 0: graph of the previous item
     const uint32_t L = a.hdr[kHdrLarge];
     const uint32_t total = a.lg_ec[L];
     constexpr int U = kEdgeChunk / kLB;
     for (uint32_t c = blockIdx.x; c < total; c += gridDim.x) {
         LargeItem it;
-        block_find(a, a.lg_ec, c, it, s_it);
+        block_find(a, a.lg_ec, c, it, s_it, hint);
         const uint32_t nn = (uint32_t)it.n;
         const uint32_t *lab = a.kl + (size_t)a.lg_vt[it.j] * kVtxTile;
         const int64_t e0 = (int64_t)it.local * kEdgeChunk;
@@ -856,12 +873,12 @@ extern "C" boba_status_t boba_reorder_batched(const int32_t *src, const int32_t 
         const int gl = bd->sms * 8;
         BOBA_TIMED("batch.small", stream,
                    k_batch_small<<<bd->grid_small, kBB, kDynSmem, stream>>>(a));
-        BOBA_TIMED("batch.large", stream, k_bl_init<<<gl, kLB, 0, stream>>>(a));
-        BOBA_TIMED("batch.large", stream, k_bl_first<<<gl, kLB, 0, stream>>>(a));
-        BOBA_TIMED("batch.large", stream, k_bl_mark<<<gl, kLB, 0, stream>>>(a));
-        BOBA_TIMED("batch.large", stream, k_bl_scan<<<gl, kLB, 0, stream>>>(a));
-        BOBA_TIMED("batch.large", stream, k_bl_emit<<<gl, kLB, 0, stream>>>(a));
-        BOBA_TIMED("batch.large", stream, k_bl_relabel<<<gl, kLB, 0, stream>>>(a));
+        BOBA_TIMED("batch.large.init", stream, k_bl_init<<<gl, kLB, 0, stream>>>(a));
+        BOBA_TIMED("batch.large.first", stream, k_bl_first<<<gl, kLB, 0, stream>>>(a));
+        BOBA_TIMED("batch.large.mark", stream, k_bl_mark<<<gl, kLB, 0, stream>>>(a));
+        BOBA_TIMED("batch.large.scan", stream, k_bl_scan<<<gl, kLB, 0, stream>>>(a));
+        BOBA_TIMED("batch.large.emit", stream, k_bl_emit<<<gl, kLB, 0, stream>>>(a));
+        BOBA_TIMED("batch.large.relabel", stream, k_bl_relabel<<<gl, kLB, 0, stream>>>(a));
     }
     BOBA_LAUNCH_CHECK();
     return BOBA_OK;
