@@ -257,12 +257,17 @@ size_t boba_reorder_batched_workspace_bytes(int64_t G, int64_t max_m, int64_t ma
 
 /*
  * boba_batched_set_mode -- how boba_reorder_batched schedules graphs above
- * 55,296 vertices: 0 = on 8-CTA clusters with the keys in distributed shared
- * memory (one persistent cluster launch for everything); 1 = all of them
- * together, phase by phase, with the keys in global memory, beside a
- * persistent one-CTA-per-graph launch for the smaller graphs (the default);
- * -1 = back to the default (or the BOBA_BATCH_MODE environment variable,
- * "cluster" or "split").  Both give identical results.  Process-wide; host only.
+ * 55,296 vertices.  0 = on 8-CTA clusters with the keys in distributed shared
+ * memory (one persistent cluster launch for everything).  1 .. 5 = all of
+ * them together, phase by phase, beside a persistent one-CTA-per-graph
+ * launch for the smaller graphs; the first-occurrence and relabel phases of
+ * a graph of up to S slices of 55,296 vertices keep its keys / labels in
+ * shared memory, one slice per CTA, each CTA streaming all of the graph's
+ * endpoints, and larger graphs use the keys in global memory.  S for the two
+ * phases: 1 (the default): 8 and 2; 2: 8 and 8; 3: 8 and none; 4: none and
+ * none; 5: 3 and none.  -1 = back to the default (the autotuned choice, or
+ * the BOBA_BATCH_MODE environment variable, "cluster" or "split").  All give
+ * identical results.  Process-wide; host only.
  */
 void boba_batched_set_mode(int mode);
 

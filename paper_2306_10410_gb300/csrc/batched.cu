@@ -48,7 +48,8 @@ constexpr size_t kDynSmem = (size_t)kKcap * 4;
 constexpr int kU = 8;                      // stream loads in flight per thread
 constexpr int64_t kSmallMaxM = 1ll << 21;  // split mode: graphs with more edges go to the phase path
 constexpr int kHdrItems = 0, kHdrLarge = 1, kHdrTicket = 2, kHdrValid = 3, kHdrScanTicket = 4,
-              kHdrEmitTicket = 5;
+              kHdrEmitTicket = 5, kHdrSliceFirst = 6, kHdrSliceRelabel = 7;
+constexpr int kMaxSlices = 8;              // sliced large path: n <= kMaxSlices * kKcap
 
 // tiles of the phase-batched large-graph path
 constexpr int kLB = 256;                   // threads per block
@@ -74,12 +75,15 @@ struct BatchArgs {
     int64_t small_max_m;     // ... and, in split mode, graphs with more edges
     int64_t n_limit;         // largest graph the mode can take
     // phase-batched large-graph path (prefix tables over the large graphs, L+1 entries)
-    uint32_t *lg_pc, *lg_vt, *lg_wt, *lg_ec, *lg_tot;
+    uint32_t *lg_pc, *lg_vt, *lg_wt, *lg_ec, *lg_tot, *lg_st;
     uint32_t *kl;            // keys, then labels, of the large graphs (vertex-tile padded)
     uint32_t *lbm;           // bitmaps of the large graphs (word-tile padded)
     uint32_t *lgrp;          // group prefixes (one per 8 words)
     uint64_t *lts_scan, *lts_emit;
     int64_t lts_scan_cap, lts_emit_cap;
+    // sliced large path: graphs of at most this many slices take the sliced
+    // first-occurrence / relabel kernel, the others the global one (0: none)
+    int first_smax, relabel_smax;
 };
 
 __device__ __forceinline__ int floor_log2_p1(int64_t x)   // floor(log2(x + 1)), x >= 0
@@ -103,7 +107,7 @@ __global__ void __launch_bounds__(1024) k_batch_plan(BatchArgs a)
 {
     __shared__ uint32_t hist[128], cur[128];
     __shared__ typename BlockScan<1024>::Smem sm;
-    __shared__ uint32_t carry[4];
+    __shared__ uint32_t carry[5];
     for (int i = threadIdx.x; i < 128; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     for (int64_t g = threadIdx.x; g < a.G; g += blockDim.x) {
@@ -128,7 +132,9 @@ __global__ void __launch_bounds__(1024) k_batch_plan(BatchArgs a)
         a.hdr[kHdrTicket] = 0;
         a.hdr[kHdrScanTicket] = 0;
         a.hdr[kHdrEmitTicket] = 0;
-        for (int k = 0; k < 4; ++k) carry[k] = 0;
+        a.hdr[kHdrSliceFirst] = 0;
+        a.hdr[kHdrSliceRelabel] = 0;
+        for (int k = 0; k < 5; ++k) carry[k] = 0;
     }
     __syncthreads();
     for (int64_t g = threadIdx.x; g < a.G; g += blockDim.x) {
@@ -143,7 +149,7 @@ __global__ void __launch_bounds__(1024) k_batch_plan(BatchArgs a)
     const uint32_t L = a.hdr[kHdrLarge];
     for (uint32_t base = 0; base <= L; base += blockDim.x) {
         const uint32_t j = base + threadIdx.x;
-        uint32_t c[4] = {0, 0, 0, 0};
+        uint32_t c[5] = {0, 0, 0, 0, 0};
         if (j < L) {
             const uint32_t g = a.order[j];
             const int64_t m = a.eoff[g + 1] - a.eoff[g], n = a.voff[g + 1] - a.voff[g];
@@ -152,9 +158,10 @@ __global__ void __launch_bounds__(1024) k_batch_plan(BatchArgs a)
             const int64_t words = cdiv(2 * m, 32) > 0 ? cdiv(2 * m, 32) : 1;
             c[2] = (uint32_t)cdiv(words, kWordTile);
             c[3] = (uint32_t)cdiv(m, kEdgeChunk);
+            c[4] = (uint32_t)cdiv(n, kKcap);
         }
-        uint32_t *tabs[4] = {a.lg_pc, a.lg_vt, a.lg_wt, a.lg_ec};
-        for (int k = 0; k < 4; ++k) {
+        uint32_t *tabs[5] = {a.lg_pc, a.lg_vt, a.lg_wt, a.lg_ec, a.lg_st};
+        for (int k = 0; k < 5; ++k) {
             uint32_t tot;
             const uint32_t ex = BlockScan<1024>::exclusive(c[k], &tot, sm);
             if (j <= L) tabs[k][j] = carry[k] + ex;
@@ -504,6 +511,7 @@ __global__ void __launch_bounds__(kLB) k_bl_first(BatchArgs a)
     for (uint32_t c = blockIdx.x; c < total; c += gridDim.x) {
         LargeItem it;
         block_find(a, a.lg_pc, c, it, s_it, hint);
+        if (cdiv(it.n, kKcap) <= a.first_smax) continue;      // done by the sliced kernel
         const uint32_t nn = (uint32_t)it.n;
         uint32_t *key = a.kl + (size_t)a.lg_vt[it.j] * kVtxTile;
         const int64_t p0 = (int64_t)it.local * kPosChunk;
@@ -657,6 +665,7 @@ __global__ void __launch_bounds__(kLB) k_bl_relabel(BatchArgs a)
     for (uint32_t c = blockIdx.x; c < total; c += gridDim.x) {
         LargeItem it;
         block_find(a, a.lg_ec, c, it, s_it, hint);
+        if (cdiv(it.n, kKcap) <= a.relabel_smax) continue;    // done by the sliced kernel
         const uint32_t nn = (uint32_t)it.n;
         const uint32_t *lab = a.kl + (size_t)a.lg_vt[it.j] * kVtxTile;
         const int64_t e0 = (int64_t)it.local * kEdgeChunk;
@@ -688,6 +697,138 @@ __global__ void __launch_bounds__(kLB) k_bl_relabel(BatchArgs a)
 }
 
 // ---------------------------------------------------------------------------
+// Sliced large path: for large graphs of at most kMaxSlices * kKcap vertices,
+// the first-occurrence and relabel phases run with the keys (labels) in
+// shared memory.  A graph's vertex range is cut into slices of kKcap; task
+// (graph, slice) is one persistent CTA's: it streams all of the graph's
+// endpoints and handles only those in its slice.  A graph's slices are
+// consecutive tasks, so they run side by side and read the same lines: the
+// streams are loaded with normal L2 priority so that only the first slice
+// reads them from DRAM.  Every key / label access is a shared-memory access
+// instead of an L1/L2 gather.  The bitmap, scan and emit phases between them are the ones above.
+// ---------------------------------------------------------------------------
+
+constexpr int kSliceU = 8;                 // int4 stream loads in flight per thread
+
+// Calls f(v, p) for every element v = X[e], e in [0, m), with p = pos0 + e:
+// a head of up to three elements to the next 16-byte boundary, the body in
+// int4 loads, and a tail of up to three.
+template <class F>
+__device__ __forceinline__ void stream_block(const int32_t *__restrict__ X, int64_t m, int64_t pos0,
+                                             F f)
+{
+    int64_t head = (int64_t)(((16u - ((uint32_t)(uintptr_t)X & 15u)) & 15u) >> 2);
+    if (head > m) head = m;
+    if (threadIdx.x < head) f(__ldcg(X + threadIdx.x), pos0 + threadIdx.x);
+    const int4 *X4 = reinterpret_cast<const int4 *>(X + head);
+    const int64_t q = (m - head) >> 2;
+    const int64_t step = (int64_t)kBB * kSliceU;
+    for (int64_t b0 = threadIdx.x; b0 < q; b0 += step) {
+        int4 w[kSliceU];
+#pragma unroll
+        for (int u = 0; u < kSliceU; ++u) {
+            const int64_t k = b0 + (int64_t)u * kBB;
+            w[u] = k < q ? __ldcg(X4 + k) : make_int4(-1, -1, -1, -1);   // kept in L2 for the sibling slices
+        }
+#pragma unroll
+        for (int u = 0; u < kSliceU; ++u) {
+            const int64_t k = b0 + (int64_t)u * kBB;
+            if (k < q) {
+                const int64_t p = pos0 + head + 4 * k;
+                f(w[u].x, p);
+                f(w[u].y, p + 1);
+                f(w[u].z, p + 2);
+                f(w[u].w, p + 3);
+            }
+        }
+    }
+    const int64_t t0 = head + 4 * q;
+    if (t0 + threadIdx.x < m) f(__ldcg(X + t0 + threadIdx.x), pos0 + t0 + threadIdx.x);
+}
+
+__global__ void __launch_bounds__(kBB, 1) k_bl_first_sliced(BatchArgs a)
+{
+    extern __shared__ uint32_t s_keys[];   // kKcap
+    __shared__ LargeItem s_it;
+    __shared__ uint32_t s_task;
+    uint32_t hint = 0;                     // thread 0: graph of the previous task
+    const uint32_t L = a.hdr[kHdrLarge];
+    const uint32_t total = a.lg_st[L];
+    while (true) {
+        if (threadIdx.x == 0) s_task = atomicAdd(&a.hdr[kHdrSliceFirst], 1u);
+        __syncthreads();
+        const uint32_t t = s_task;
+        if (t >= total) break;
+        LargeItem it;
+        block_find(a, a.lg_st, t, it, s_it, hint);
+        if (cdiv(it.n, kKcap) > a.first_smax) continue;       // done by the global kernel
+        const uint32_t base = it.local * (uint32_t)kKcap;
+        const uint32_t cnt = (uint32_t)min((int64_t)kKcap, it.n - base);
+        for (uint32_t i = threadIdx.x; i < cnt; i += kBB) s_keys[i] = kSent;
+        __syncthreads();
+        const uint32_t nn = (uint32_t)it.n;
+        const bool first_slice = it.local == 0;
+        auto visit = [&](int32_t v, int64_t p) {
+            const uint32_t u = (uint32_t)v - base;
+            if (u < cnt) {
+                if (s_keys[u] > (uint32_t)p) atomicMin(&s_keys[u], (uint32_t)p);
+            } else if ((uint32_t)v >= nn && first_slice) {
+                raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
+            }
+        };
+        stream_block(a.src + it.E0, it.m, 0, visit);          // positions 0 .. m-1
+        stream_block(a.dst + it.E0, it.m, it.m, visit);       // positions m .. 2m-1
+        __syncthreads();
+        uint32_t *key = a.kl + (size_t)a.lg_vt[it.j] * kVtxTile + base;
+        for (uint32_t i = threadIdx.x; i < cnt; i += kBB) key[i] = s_keys[i];
+        __syncthreads();                   // s_keys and s_task are reused
+    }
+}
+
+__global__ void __launch_bounds__(kBB, 1) k_bl_relabel_sliced(BatchArgs a)
+{
+    extern __shared__ uint32_t s_lab[];    // kKcap
+    __shared__ LargeItem s_it;
+    __shared__ uint32_t s_task;
+    uint32_t hint = 0;
+    const uint32_t L = a.hdr[kHdrLarge];
+    const uint32_t total = a.lg_st[L];
+    while (true) {
+        if (threadIdx.x == 0) s_task = atomicAdd(&a.hdr[kHdrSliceRelabel], 1u);
+        __syncthreads();
+        const uint32_t t = s_task;
+        if (t >= total) break;
+        LargeItem it;
+        block_find(a, a.lg_st, t, it, s_it, hint);
+        if (cdiv(it.n, kKcap) > a.relabel_smax) continue;     // done by the global kernel
+        const uint32_t base = it.local * (uint32_t)kKcap;
+        const uint32_t cnt = (uint32_t)min((int64_t)kKcap, it.n - base);
+        const uint32_t *lab = a.kl + (size_t)a.lg_vt[it.j] * kVtxTile + base;
+        for (uint32_t i = threadIdx.x; i < cnt; i += kBB) s_lab[i] = __ldcg(lab + i);
+        __syncthreads();
+        const uint32_t nn = (uint32_t)it.n;
+        const bool first_slice = it.local == 0;
+        // each output element is written by the one task whose slice holds its
+        // vertex (an ID outside [0, n) by the first slice, as -1)
+        auto out = [&](int32_t *o) {
+            return [&, o](int32_t v, int64_t e) {
+                const uint32_t u = (uint32_t)v - base;
+                // plain stores: the slices' partial writes of one line merge in L2
+                if (u < cnt) {
+                    o[e] = (int32_t)s_lab[u];
+                } else if ((uint32_t)v >= nn && first_slice) {
+                    raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
+                    o[e] = -1;
+                }
+            };
+        };
+        stream_block(a.src + it.E0, it.m, 0, out(a.so + it.E0));
+        stream_block(a.dst + it.E0, it.m, 0, out(a.dout + it.E0));
+        __syncthreads();                   // s_lab and s_task are reused
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 
@@ -714,6 +855,12 @@ const BatchDevice *batch_device()
         if (cudaFuncSetAttribute((const void *)k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kDynSmem) != cudaSuccess ||
             cudaFuncSetAttribute((const void *)k_batch_small,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kDynSmem) != cudaSuccess ||
+            cudaFuncSetAttribute((const void *)k_bl_first_sliced,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kDynSmem) != cudaSuccess ||
+            cudaFuncSetAttribute((const void *)k_bl_relabel_sliced,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kDynSmem) != cudaSuccess ||
             cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -747,12 +894,32 @@ const BatchDevice *batch_device()
 // environment, else split.
 int batch_mode(int64_t total_m)
 {
-    if (g_mode_override >= 0) return g_mode_override;
-    const int v = tuned_variant(kTuneBatched, total_m);      // 0 split, 1 cluster
+    if (g_mode_override >= 0) return g_mode_override == 0 ? kBatchCluster : kBatchSplit;
+    const int v = tuned_variant(kTuneBatched, total_m);      // 0 split, 1 cluster, 2 split+sliced
     if (v == 1) return kBatchCluster;
     const char *e = getenv("BOBA_BATCH_MODE");
     if (v == 0 && e && strcmp(e, "cluster") == 0) return kBatchCluster;
     return kBatchSplit;
+}
+
+// Split mode: up to how many slices a large graph takes the sliced
+// first-occurrence (fs) and relabel (rs) kernel instead of the global one.
+// Schedules (the numbers of boba_batched_set_mode; the tuner's variants are
+// the same except that its 0 is schedule 1 and its 1 is schedule 0):
+//   1: fs 8, rs 2 (the default: measured best on the 4096-graph batch)
+//   2: fs 8, rs 8     3: fs 8, rs 0     4: global phases only     5: fs 3, rs 0
+void batch_slices(int64_t total_m, int &fs, int &rs)
+{
+    int sched = g_mode_override;
+    if (sched < 0) {
+        const int v = tuned_variant(kTuneBatched, total_m);
+        sched = v == 0 ? 1 : v == 1 ? 0 : v;
+    }
+    fs = rs = 0;
+    if (sched == 1) { fs = kMaxSlices; rs = 2; }
+    else if (sched == 2) { fs = kMaxSlices; rs = kMaxSlices; }
+    else if (sched == 3) { fs = kMaxSlices; }
+    else if (sched == 5) { fs = 3; }
 }
 
 struct BatchLayout {
@@ -778,7 +945,7 @@ bool batch_layout(int64_t G, int64_t max_m, int64_t max_n, int64_t total_m, int6
     L.hdr = c.take(64);
     L.order = c.take((size_t)(G > 0 ? G : 1) * 4);
     L.scratch = c.take((size_t)L.regions * L.region_words * 4);
-    L.tabs = c.take((size_t)5 * (G + 1) * 4);
+    L.tabs = c.take((size_t)6 * (G + 1) * 4);
     L.kl = c.take((size_t)L.lvt_cap * kVtxTile * 4);
     L.lbm = c.take((size_t)L.lwt_cap * kWordTile * 4);
     L.lgrp = c.take((size_t)L.lwt_cap * kWordTile / 8 * 4);
@@ -857,6 +1024,7 @@ extern "C" boba_status_t boba_reorder_batched(const int32_t *src, const int32_t 
         a.lg_wt = tabs + 2 * (G + 1);
         a.lg_ec = tabs + 3 * (G + 1);
         a.lg_tot = tabs + 4 * (G + 1);
+        a.lg_st = tabs + 5 * (G + 1);
         a.kl = reinterpret_cast<uint32_t *>(b + L.kl);
         a.lbm = reinterpret_cast<uint32_t *>(b + L.lbm);
         a.lgrp = reinterpret_cast<uint32_t *>(b + L.lgrp);
@@ -864,6 +1032,7 @@ extern "C" boba_status_t boba_reorder_batched(const int32_t *src, const int32_t 
         a.lts_emit = reinterpret_cast<uint64_t *>(b + L.lts_emit);
         a.lts_scan_cap = L.lwt_cap;
         a.lts_emit_cap = L.lvt_cap;
+        batch_slices(total_m, a.first_smax, a.relabel_smax);
     }
     BOBA_TIMED("batch.plan", stream, k_batch_plan<<<1, 1024, 0, stream>>>(a));
     if (mode == kBatchCluster) {
@@ -874,15 +1043,28 @@ extern "C" boba_status_t boba_reorder_batched(const int32_t *src, const int32_t 
         BOBA_TIMED("batch.small", stream,
                    k_batch_small<<<bd->grid_small, kBB, kDynSmem, stream>>>(a));
         BOBA_TIMED("batch.large.init", stream, k_bl_init<<<gl, kLB, 0, stream>>>(a));
-        BOBA_TIMED("batch.large.first", stream, k_bl_first<<<gl, kLB, 0, stream>>>(a));
+        // graphs of up to fs (rs) slices: sliced kernels; the rest: global ones
+        if (a.first_smax > 0)
+            BOBA_TIMED("batch.large.first", stream,
+                       k_bl_first_sliced<<<bd->grid_small, kBB, kDynSmem, stream>>>(a));
+        if (max_n > (int64_t)a.first_smax * kKcap)
+            BOBA_TIMED("batch.large.first", stream, k_bl_first<<<gl, kLB, 0, stream>>>(a));
         BOBA_TIMED("batch.large.mark", stream, k_bl_mark<<<gl, kLB, 0, stream>>>(a));
         BOBA_TIMED("batch.large.scan", stream, k_bl_scan<<<gl, kLB, 0, stream>>>(a));
         BOBA_TIMED("batch.large.emit", stream, k_bl_emit<<<gl, kLB, 0, stream>>>(a));
-        BOBA_TIMED("batch.large.relabel", stream, k_bl_relabel<<<gl, kLB, 0, stream>>>(a));
+        if (a.relabel_smax > 0)
+            BOBA_TIMED("batch.large.relabel", stream,
+                       k_bl_relabel_sliced<<<bd->grid_small, kBB, kDynSmem, stream>>>(a));
+        if (max_n > (int64_t)a.relabel_smax * kKcap)
+            BOBA_TIMED("batch.large.relabel", stream, k_bl_relabel<<<gl, kLB, 0, stream>>>(a));
     }
     BOBA_LAUNCH_CHECK();
     return BOBA_OK;
 }
 
-// Selects the batched mode explicitly (autotuner hook): 0 cluster, 1 split, -1 default.
-extern "C" void boba_batched_set_mode(int mode) { g_mode_override = (mode == 0 || mode == 1) ? mode : -1; }
+// Selects the batched schedule explicitly: 0 cluster, 1 .. 5 split with the
+// large-graph phases as batch_slices lists, -1 default.
+extern "C" void boba_batched_set_mode(int mode)
+{
+    g_mode_override = (mode >= 0 && mode <= 5) ? mode : -1;
+}

@@ -21,7 +21,9 @@ def boba():
     b.boba_batched_set_mode(-1)
 
 
-MODES = [pytest.param(0, id="cluster"), pytest.param(1, id="split")]
+MODES = [pytest.param(0, id="cluster"), pytest.param(1, id="split"),
+         pytest.param(2, id="sliced"), pytest.param(3, id="sliced_first"),
+         pytest.param(4, id="global"), pytest.param(5, id="sliced_small")]
 
 
 def pack(graphs):
@@ -142,8 +144,9 @@ def test_size_limits(boba):
     assert boba.boba_reorder_batched_workspace_bytes(4096, 1 << 23, TEAM_MAX, 1 << 31, 1 << 28) > 0
 
 
-def test_split_mode_takes_graphs_beyond_cluster_capacity(boba):
-    boba.boba_batched_set_mode(1)
+@pytest.mark.parametrize("mode", [1, 2, 4])
+def test_split_mode_takes_graphs_beyond_cluster_capacity(boba, mode):
+    boba.boba_batched_set_mode(mode)           # the largest go to the global phases
     graphs = []
     for n, m, seed in ((TEAM_MAX + 5000, 900_000, 21), (3000, 40_000, 22), (1 << 20, 3_000_000, 23),
                        (50_000, 2_500_000, 24)):                 # last: small n, many edges
@@ -166,11 +169,14 @@ def test_full_batch_4096_graphs(boba):
     eo_d, vo_d = torch.from_numpy(eo).cuda(), torch.from_numpy(vo).cuda()
     boba.boba_batched_set_mode(0)
     perm0, so0, do0 = boba.reorder_batched(s_d, d_d, eo_d, vo_d)
+    boba.boba_batched_set_mode(4)            # global large phases only
+    perm2, so2, do2 = boba.reorder_batched(s_d, d_d, eo_d, vo_d)
     boba.boba_batched_set_mode(1)
     perm, so, do = boba.reorder_batched(s_d, d_d, eo_d, vo_d)
     boba.stream_status()
     assert torch.equal(perm0, perm) and torch.equal(so0, so) and torch.equal(do0, do)
-    del perm0, so0, do0
+    assert torch.equal(perm2, perm) and torch.equal(so2, so) and torch.equal(do2, do)
+    del perm0, so0, do0, perm2, so2, do2
     for g in range(G):
         n = int(vo[g + 1] - vo[g])
         p1, s1, d1 = boba.reorder(s_d[eo[g]:eo[g + 1]], d_d[eo[g]:eo[g + 1]], n)
