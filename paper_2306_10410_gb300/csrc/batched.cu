@@ -53,10 +53,10 @@ constexpr int kMaxSlices = 8;              // sliced large path: n <= kMaxSlices
 
 // tiles of the phase-batched large-graph path
 constexpr int kLB = 256;                   // threads per block
-constexpr int kPosChunk = kLB * 16;        // positions of I ++ J per block step
+constexpr int kPosChunk = kLB * 64;        // positions of I ++ J per block step (4 rounds of 16)
 constexpr int kVtxTile = kLB * 4;          // vertices per tile
 constexpr int kWordTile = kLB * 8;         // bitmap words per scan tile
-constexpr int kEdgeChunk = kLB * 8;        // edges per relabel block step
+constexpr int kEdgeChunk = kLB * 32;       // edges per relabel block step (4 rounds of 8 per thread)
 
 enum BatchMode { kBatchCluster = 0, kBatchSplit = 1 };
 
@@ -507,31 +507,34 @@ __global__ void __launch_bounds__(kLB) k_bl_first(BatchArgs a)
     uint32_t hint = 0;                     // thread 0: graph of the previous item
     const uint32_t L = a.hdr[kHdrLarge];
     const uint32_t total = a.lg_pc[L];
-    constexpr int U = kPosChunk / kLB;
+    constexpr int U = 16;                  // positions per thread per round
     for (uint32_t c = blockIdx.x; c < total; c += gridDim.x) {
         LargeItem it;
         block_find(a, a.lg_pc, c, it, s_it, hint);
         if (cdiv(it.n, kKcap) <= a.first_smax) continue;      // done by the sliced kernel
         const uint32_t nn = (uint32_t)it.n;
         uint32_t *key = a.kl + (size_t)a.lg_vt[it.j] * kVtxTile;
-        const int64_t p0 = (int64_t)it.local * kPosChunk;
-        const int64_t p1 = min(p0 + (int64_t)kPosChunk, 2 * it.m);
-        int32_t v[U];
+        const int64_t c0 = (int64_t)it.local * kPosChunk;
+        const int64_t p1 = min(c0 + (int64_t)kPosChunk, 2 * it.m);
+        for (int64_t p0 = c0; p0 < p1; p0 += (int64_t)U * kLB) {
+            int32_t v[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t i = p0 + u * kLB + threadIdx.x;
-            v[u] = -1;
-            if (i < p1) v[u] = i < it.m ? __ldcs(a.src + it.E0 + i) : __ldcs(a.dst + it.E0 + (i - it.m));
-        }
-        uint32_t cur[U];
+            for (int u = 0; u < U; ++u) {
+                const int64_t i = p0 + u * kLB + threadIdx.x;
+                v[u] = -1;
+                if (i < p1)
+                    v[u] = i < it.m ? __ldcs(a.src + it.E0 + i) : __ldcs(a.dst + it.E0 + (i - it.m));
+            }
+            uint32_t cur[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) cur[u] = (uint32_t)v[u] < nn ? key[v[u]] : 0u;
+            for (int u = 0; u < U; ++u) cur[u] = (uint32_t)v[u] < nn ? key[v[u]] : 0u;
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t i = p0 + u * kLB + threadIdx.x;
-            if (i >= p1) continue;
-            if ((uint32_t)v[u] >= nn) raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
-            else if (cur[u] > (uint32_t)i) atomicMin(&key[v[u]], (uint32_t)i);
+            for (int u = 0; u < U; ++u) {
+                const int64_t i = p0 + u * kLB + threadIdx.x;
+                if (i >= p1) continue;
+                if ((uint32_t)v[u] >= nn) raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
+                else if (cur[u] > (uint32_t)i) atomicMin(&key[v[u]], (uint32_t)i);
+            }
         }
     }
 }
@@ -661,37 +664,39 @@ __global__ void __launch_bounds__(kLB) k_bl_relabel(BatchArgs a)
     uint32_t hint = 0;                     // thread 0: graph of the previous item
     const uint32_t L = a.hdr[kHdrLarge];
     const uint32_t total = a.lg_ec[L];
-    constexpr int U = kEdgeChunk / kLB;
+    constexpr int U = 8;                   // edges per thread per round
     for (uint32_t c = blockIdx.x; c < total; c += gridDim.x) {
         LargeItem it;
         block_find(a, a.lg_ec, c, it, s_it, hint);
         if (cdiv(it.n, kKcap) <= a.relabel_smax) continue;    // done by the sliced kernel
         const uint32_t nn = (uint32_t)it.n;
         const uint32_t *lab = a.kl + (size_t)a.lg_vt[it.j] * kVtxTile;
-        const int64_t e0 = (int64_t)it.local * kEdgeChunk;
-        const int64_t e1 = min(e0 + (int64_t)kEdgeChunk, it.m);
-        int32_t s[U], d[U];
+        const int64_t c0 = (int64_t)it.local * kEdgeChunk;
+        const int64_t c1 = min(c0 + (int64_t)kEdgeChunk, it.m);
+        for (int64_t e0 = c0; e0 < c1; e0 += (int64_t)U * kLB) {
+            int32_t s[U], d[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t e = e0 + u * kLB + threadIdx.x;
-            s[u] = d[u] = -1;
-            if (e < e1) {
-                s[u] = __ldcs(a.src + it.E0 + e);
-                d[u] = __ldcs(a.dst + it.E0 + e);
+            for (int u = 0; u < U; ++u) {
+                const int64_t e = e0 + u * kLB + threadIdx.x;
+                s[u] = d[u] = -1;
+                if (e < c1) {
+                    s[u] = __ldcs(a.src + it.E0 + e);
+                    d[u] = __ldcs(a.dst + it.E0 + e);
+                }
             }
-        }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            s[u] = (uint32_t)s[u] < nn ? (int32_t)__ldg(lab + s[u]) : -1;
-            d[u] = (uint32_t)d[u] < nn ? (int32_t)__ldg(lab + d[u]) : -1;
-        }
+            for (int u = 0; u < U; ++u) {
+                s[u] = (uint32_t)s[u] < nn ? (int32_t)__ldg(lab + s[u]) : -1;
+                d[u] = (uint32_t)d[u] < nn ? (int32_t)__ldg(lab + d[u]) : -1;
+            }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t e = e0 + u * kLB + threadIdx.x;
-            if (e >= e1) continue;
-            if (s[u] < 0 || d[u] < 0) raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
-            __stcs(a.so + it.E0 + e, s[u]);
-            __stcs(a.dout + it.E0 + e, d[u]);
+            for (int u = 0; u < U; ++u) {
+                const int64_t e = e0 + u * kLB + threadIdx.x;
+                if (e >= c1) continue;
+                if (s[u] < 0 || d[u] < 0) raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
+                __stcs(a.so + it.E0 + e, s[u]);
+                __stcs(a.dout + it.E0 + e, d[u]);
+            }
         }
     }
 }
@@ -906,8 +911,8 @@ int batch_mode(int64_t total_m)
 // first-occurrence (fs) and relabel (rs) kernel instead of the global one.
 // Schedules (the numbers of boba_batched_set_mode; the tuner's variants are
 // the same except that its 0 is schedule 1 and its 1 is schedule 0):
-//   1: fs 8, rs 2 (the default: measured best on the 4096-graph batch)
-//   2: fs 8, rs 8     3: fs 8, rs 0     4: global phases only     5: fs 3, rs 0
+//   1: fs 8, rs 0 (the default: measured best on the 4096-graph batch)
+//   2: fs 8, rs 8     3: fs 8, rs 2     4: global phases only     5: fs 3, rs 0
 void batch_slices(int64_t total_m, int &fs, int &rs)
 {
     int sched = g_mode_override;
@@ -916,9 +921,9 @@ void batch_slices(int64_t total_m, int &fs, int &rs)
         sched = v == 0 ? 1 : v == 1 ? 0 : v;
     }
     fs = rs = 0;
-    if (sched == 1) { fs = kMaxSlices; rs = 2; }
+    if (sched == 1) { fs = kMaxSlices; }
     else if (sched == 2) { fs = kMaxSlices; rs = kMaxSlices; }
-    else if (sched == 3) { fs = kMaxSlices; }
+    else if (sched == 3) { fs = kMaxSlices; rs = 2; }
     else if (sched == 5) { fs = 3; }
 }
 

@@ -22,7 +22,7 @@ def boba():
 
 
 MODES = [pytest.param(0, id="cluster"), pytest.param(1, id="split"),
-         pytest.param(2, id="sliced"), pytest.param(3, id="sliced_first"),
+         pytest.param(2, id="sliced"), pytest.param(3, id="sliced_mixed"),
          pytest.param(4, id="global"), pytest.param(5, id="sliced_small")]
 
 
