@@ -563,6 +563,10 @@ def run_batched(args, boba, torch, dev, stream, flush, n_batch=4096, seed=None):
             "max_m": max_m, "max_n": max_n,
             "batched_ms": round(t_batched, 3),
             "batched_gedges_s": round(E / (t_batched * 1e-3) / 1e9, 3),
+            "roofline": {"alg_bytes": 24 * E + 4 * V,
+                         "achieved_gbs": round((24 * E + 4 * V) / (t_batched * 1e-3) / 1e9, 1),
+                         "frac": round((24 * E + 4 * V) / (t_batched * 1e-3) / 1e9
+                                       / peaks()[0], 4)},
             "per_graph_ms": round(t_pergraph, 3),
             "per_graph_gedges_s": round(E / (t_pergraph * 1e-3) / 1e9, 3),
             "speedup_batched_vs_per_graph": round(t_pergraph / t_batched, 3),
