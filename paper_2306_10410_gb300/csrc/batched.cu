@@ -717,38 +717,41 @@ constexpr int kSliceU = 8;                 // int4 stream loads in flight per th
 
 // Calls f(v, p) for every element v = X[e], e in [0, m), with p = pos0 + e:
 // a head of up to three elements to the next 16-byte boundary, the body in
-// int4 loads, and a tail of up to three.
+// int4 loads, and a tail of up to three.  Indices and positions fit in 32
+// bits (2m < 2^32), which keeps the per-element work short.
 template <class F>
 __device__ __forceinline__ void stream_block(const int32_t *__restrict__ X, int64_t m, int64_t pos0,
                                              F f)
 {
-    int64_t head = (int64_t)(((16u - ((uint32_t)(uintptr_t)X & 15u)) & 15u) >> 2);
-    if (head > m) head = m;
-    if (threadIdx.x < head) f(__ldcg(X + threadIdx.x), pos0 + threadIdx.x);
+    const uint32_t mm = (uint32_t)m, p0 = (uint32_t)pos0;
+    uint32_t head = ((16u - ((uint32_t)(uintptr_t)X & 15u)) & 15u) >> 2;
+    if (head > mm) head = mm;
+    if (threadIdx.x < head) f(__ldcg(X + threadIdx.x), p0 + threadIdx.x);
     const int4 *X4 = reinterpret_cast<const int4 *>(X + head);
-    const int64_t q = (m - head) >> 2;
-    const int64_t step = (int64_t)kBB * kSliceU;
-    for (int64_t b0 = threadIdx.x; b0 < q; b0 += step) {
+    const uint32_t q = (mm - head) >> 2;
+    const uint32_t pb = p0 + head;
+    constexpr uint32_t step = (uint32_t)kBB * kSliceU;
+    for (uint32_t b0 = threadIdx.x; b0 < q; b0 += step) {
         int4 w[kSliceU];
 #pragma unroll
         for (int u = 0; u < kSliceU; ++u) {
-            const int64_t k = b0 + (int64_t)u * kBB;
+            const uint32_t k = b0 + (uint32_t)u * kBB;
             w[u] = k < q ? __ldcg(X4 + k) : make_int4(-1, -1, -1, -1);   // kept in L2 for the sibling slices
         }
 #pragma unroll
         for (int u = 0; u < kSliceU; ++u) {
-            const int64_t k = b0 + (int64_t)u * kBB;
+            const uint32_t k = b0 + (uint32_t)u * kBB;
             if (k < q) {
-                const int64_t p = pos0 + head + 4 * k;
+                const uint32_t p = pb + 4u * k;
                 f(w[u].x, p);
-                f(w[u].y, p + 1);
-                f(w[u].z, p + 2);
-                f(w[u].w, p + 3);
+                f(w[u].y, p + 1u);
+                f(w[u].z, p + 2u);
+                f(w[u].w, p + 3u);
             }
         }
     }
-    const int64_t t0 = head + 4 * q;
-    if (t0 + threadIdx.x < m) f(__ldcg(X + t0 + threadIdx.x), pos0 + t0 + threadIdx.x);
+    const uint32_t t0 = head + 4u * q;
+    if (t0 + threadIdx.x < mm) f(__ldcg(X + t0 + threadIdx.x), p0 + t0 + threadIdx.x);
 }
 
 __global__ void __launch_bounds__(kBB, 1) k_bl_first_sliced(BatchArgs a)
@@ -772,17 +775,19 @@ __global__ void __launch_bounds__(kBB, 1) k_bl_first_sliced(BatchArgs a)
         for (uint32_t i = threadIdx.x; i < cnt; i += kBB) s_keys[i] = kSent;
         __syncthreads();
         const uint32_t nn = (uint32_t)it.n;
-        const bool first_slice = it.local == 0;
-        auto visit = [&](int32_t v, int64_t p) {
+        bool bad = false;
+        // few branches per element: most endpoints belong to other slices,
+        // and divergent branches cost more here than the predicated load
+        auto visit = [&](int32_t v, uint32_t p) {
             const uint32_t u = (uint32_t)v - base;
-            if (u < cnt) {
-                if (s_keys[u] > (uint32_t)p) atomicMin(&s_keys[u], (uint32_t)p);
-            } else if ((uint32_t)v >= nn && first_slice) {
-                raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
-            }
+            const bool own = u < cnt;
+            const uint32_t cur = own ? s_keys[u] : 0u;
+            if (own && cur > p) atomicMin(&s_keys[u], p);
+            bad |= (uint32_t)v >= nn;
         };
         stream_block(a.src + it.E0, it.m, 0, visit);          // positions 0 .. m-1
         stream_block(a.dst + it.E0, it.m, it.m, visit);       // positions m .. 2m-1
+        if (bad && it.local == 0) raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
         __syncthreads();
         uint32_t *key = a.kl + (size_t)a.lg_vt[it.j] * kVtxTile + base;
         for (uint32_t i = threadIdx.x; i < cnt; i += kBB) key[i] = s_keys[i];
@@ -813,22 +818,22 @@ __global__ void __launch_bounds__(kBB, 1) k_bl_relabel_sliced(BatchArgs a)
         __syncthreads();
         const uint32_t nn = (uint32_t)it.n;
         const bool first_slice = it.local == 0;
+        bool bad = false;
         // each output element is written by the one task whose slice holds its
-        // vertex (an ID outside [0, n) by the first slice, as -1)
+        // vertex (an ID outside [0, n) by the first slice, as -1); plain
+        // stores, so that the slices' partial writes of one line merge in L2
         auto out = [&](int32_t *o) {
-            return [&, o](int32_t v, int64_t e) {
+            return [&, o](int32_t v, uint32_t e) {
                 const uint32_t u = (uint32_t)v - base;
-                // plain stores: the slices' partial writes of one line merge in L2
-                if (u < cnt) {
-                    o[e] = (int32_t)s_lab[u];
-                } else if ((uint32_t)v >= nn && first_slice) {
-                    raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
-                    o[e] = -1;
-                }
+                const bool own = u < cnt;
+                const bool oob = (uint32_t)v >= nn;
+                bad |= oob;
+                if (own || (oob && first_slice)) o[e] = own ? (int32_t)s_lab[u] : -1;
             };
         };
         stream_block(a.src + it.E0, it.m, 0, out(a.so + it.E0));
         stream_block(a.dst + it.E0, it.m, 0, out(a.dout + it.E0));
+        if (bad && first_slice) raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
         __syncthreads();                   // s_lab and s_task are reused
     }
 }
