@@ -225,6 +225,7 @@ __device__ void process_graph(const BatchArgs &a, uint32_t g, int t, int64_t cta
     // 2. first occurrence over this member's share of I ++ J: kU loads in
     // flight per thread, then all key reads, then the (rare) atomics
     {
+        bool bad = false;
         const int64_t P = 2 * m;
         const int64_t lo = P * t / T, hi = P * (t + 1) / T;
         for (int64_t b0 = lo + tid; b0 < hi; b0 += (int64_t)kU * kBB) {
@@ -239,18 +240,17 @@ __device__ void process_graph(const BatchArgs &a, uint32_t g, int t, int64_t cta
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
                 const int64_t i = b0 + (int64_t)u * kBB;
-                own[u] = kTeam;                                  // "skip"
-                li[u] = 0;
-                cur[u] = 0;
-                if (i < hi) {
-                    if ((uint32_t)v[u] < nn) {
-                        own[u] = (uint32_t)v[u] / chunk;
-                        li[u] = (uint32_t)v[u] - own[u] * chunk;
-                        cur[u] = key_ptr<T>(s_keys, ts, own[u])[li[u]];
-                    } else {
-                        raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
-                    }
+                // predicates rather than branches; one CTA owns every vertex
+                const bool ok = i < hi && (uint32_t)v[u] < nn;
+                bad |= i < hi && !ok;
+                if constexpr (T == 1) {
+                    own[u] = ok ? 0u : (uint32_t)kTeam;          // kTeam: "skip"
+                    li[u] = (uint32_t)v[u];
+                } else {
+                    own[u] = ok ? (uint32_t)v[u] / chunk : (uint32_t)kTeam;
+                    li[u] = (uint32_t)v[u] - own[u] * chunk;
                 }
+                cur[u] = ok ? key_ptr<T>(s_keys, ts, own[u])[li[u]] : 0u;
             }
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
@@ -258,6 +258,7 @@ __device__ void process_graph(const BatchArgs &a, uint32_t g, int t, int64_t cta
                 if (own[u] < kTeam && cur[u] > i) atomicMin(key_ptr<T>(s_keys, ts, own[u]) + li[u], i);
             }
         }
+        if (bad) raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
     }
     team_sync<T>(cl);
 
@@ -374,11 +375,13 @@ __device__ void process_graph(const BatchArgs &a, uint32_t g, int t, int64_t cta
             int32_t lab[kU];
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                lab[u] = -1;
-                if ((uint32_t)v[u] < nn) {
-                    const uint32_t o = (uint32_t)v[u] / chunk;
-                    lab[u] = (int32_t)key_ptr<T>(s_keys, ts, o)[(uint32_t)v[u] - o * chunk];
+                const bool ok = (uint32_t)v[u] < nn;
+                uint32_t o = 0, l = (uint32_t)v[u];
+                if constexpr (T > 1) {
+                    o = ok ? (uint32_t)v[u] / chunk : 0u;
+                    l = (uint32_t)v[u] - o * chunk;
                 }
+                lab[u] = ok ? (int32_t)key_ptr<T>(s_keys, ts, o)[l] : -1;
             }
 #pragma unroll
             for (int u = 0; u < U2; ++u) {
