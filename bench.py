@@ -572,7 +572,7 @@ def run_batched(args, boba, torch, dev, stream, flush, n_batch=4096, seed=None):
             "speedup_batched_vs_per_graph": round(t_pergraph / t_batched, 3),
             "kernels_ms": split,
             "cuda_graph_ms": t_graph,
-            "schedule": {0: "split, sliced first <= 8 slices", 1: "cluster",
+            "schedule": {0: "split, sliced first <= 8 slices, relabel <= 1", 1: "cluster",
                          2: "split, sliced first and relabel <= 8 slices",
                          3: "split, sliced first <= 8 slices, relabel <= 2",
                          4: "split, global phases", 5: "split, sliced first <= 3 slices"}.get(

@@ -264,7 +264,7 @@ size_t boba_reorder_batched_workspace_bytes(int64_t G, int64_t max_m, int64_t ma
  * a graph of up to S slices of 55,296 vertices keep its keys / labels in
  * shared memory, one slice per CTA, each CTA streaming all of the graph's
  * endpoints, and larger graphs use the keys in global memory.  S for the two
- * phases: 1 (the default): 8 and none; 2: 8 and 8; 3: 8 and 2; 4: none and
+ * phases: 1 (the default): 8 and 1; 2: 8 and 8; 3: 8 and 2; 4: none and
  * none; 5: 3 and none.  -1 = back to the default (the autotuned choice, or
  * the BOBA_BATCH_MODE environment variable, "cluster" or "split").  All give
  * identical results.  Process-wide; host only.

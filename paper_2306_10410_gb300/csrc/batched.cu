@@ -919,7 +919,8 @@ int batch_mode(int64_t total_m)
 // first-occurrence (fs) and relabel (rs) kernel instead of the global one.
 // Schedules (the numbers of boba_batched_set_mode; the tuner's variants are
 // the same except that its 0 is schedule 1 and its 1 is schedule 0):
-//   1: fs 8, rs 0 (the default: measured best on the 4096-graph batch)
+//   1: fs 8, rs 1 (the default: measured best on the 4096-graph batch; a
+//      one-slice graph relabels without redundant streams or partial writes)
 //   2: fs 8, rs 8     3: fs 8, rs 2     4: global phases only     5: fs 3, rs 0
 void batch_slices(int64_t total_m, int &fs, int &rs)
 {
@@ -929,7 +930,7 @@ void batch_slices(int64_t total_m, int &fs, int &rs)
         sched = v == 0 ? 1 : v == 1 ? 0 : v;
     }
     fs = rs = 0;
-    if (sched == 1) { fs = kMaxSlices; }
+    if (sched == 1) { fs = kMaxSlices; rs = 1; }
     else if (sched == 2) { fs = kMaxSlices; rs = kMaxSlices; }
     else if (sched == 3) { fs = kMaxSlices; rs = 2; }
     else if (sched == 5) { fs = 3; }
