@@ -424,3 +424,59 @@ def test_pagerank_planted_mistakes_fail_the_eigen_pin():
     assert np.abs(power(I, J, outdeg, False) - want).max() > 1e-3
     assert np.abs(power(I, J, np.maximum(indeg, 1), True) - want).max() > 1e-3
     assert np.abs(power(J, I, np.bincount(J, minlength=n), True) - want).max() > 1e-3
+
+
+# --- theory of Sec. 4.1 and 4.4 (informational: they check the paper's claims) ---
+
+def nscore(adj, p):
+    """NScore(G, p) = sum over consecutive p_i, p_{i+1} of |N(p_i) & N(p_{i+1})| (Sec. 4.1)."""
+    return sum(len(adj[p[i]] & adj[p[i + 1]]) for i in range(len(p) - 1))
+
+
+def small_regular_graphs():
+    """(name, undirected edges, n, d) for d-regular graphs with n <= 8."""
+    out = [(f"C{n}", [(i, (i + 1) % n) for i in range(n)], n, 2) for n in range(5, 9)]
+    out.append(("K4", [(a, b) for a in range(4) for b in range(a + 1, 4)], 4, 3))
+    out.append(("K33", [(a, b) for a in range(3) for b in range(3, 6)], 6, 3))
+    out.append(("Q3", [(a, a ^ (1 << k)) for a in range(8) for k in range(3) if a < a ^ (1 << k)],
+                8, 3))
+    out.append(("K5", [(a, b) for a in range(5) for b in range(a + 1, 5)], 5, 4))
+    out.append(("K44", [(a, b) for a in range(4) for b in range(4, 8)], 8, 4))
+    return out
+
+
+def adjacency(edges, n):
+    adj = [set() for _ in range(n)]
+    for u, v in edges:
+        adj[u].add(v)
+        adj[v].add(u)
+    return adj
+
+
+def best_nscore(adj, n):
+    return max(nscore(adj, p) for p in itertools.permutations(range(n)))
+
+
+def test_lemma1_bound_is_the_degree_sum():
+    """Lemma 1: NScore(G, p*) <= m.  The proof bounds the sum by the degree sum,
+    which is 2|E| for an undirected graph (its COO lists both directions); with
+    m = |E| the statement fails, e.g. on K3,3 (p* scores 12, |E| = 9)."""
+    for name, edges, n, _ in small_regular_graphs():
+        adj = adjacency(edges, n)
+        best = best_nscore(adj, n)
+        assert best <= sum(len(a) for a in adj), name
+    k33 = [(a, b) for a in range(3) for b in range(3, 6)]
+    assert best_nscore(adjacency(k33, 6), 6) == 12 > len(k33)
+
+
+def test_prop1_regular_graph_sorted_by_destination():
+    """Prop. 1: for a d-regular graph whose COO is sorted by destination, the
+    BOBA order scores at least 1/(d+1) of the optimum (checked by brute force)."""
+    for name, edges, n, d in small_regular_graphs():
+        arcs = sorted([(u, v) for u, v in edges] + [(v, u) for u, v in edges],
+                      key=lambda a: (a[1], a[0]))
+        I = np.array([a[0] for a in arcs], np.int32)
+        J = np.array([a[1] for a in arcs], np.int32)
+        perm, _ = oracle.boba_perm(I, J, n)
+        adj = adjacency(edges, n)
+        assert (d + 1) * nscore(adj, list(perm)) >= best_nscore(adj, n), name
