@@ -313,6 +313,15 @@ int64_t boba_server_submit(boba_server_t *server, const int32_t *src, const int3
 int boba_server_poll(boba_server_t *server, int64_t *ids, double *latency_ms, int *status,
                      int cap);
 
+/*
+ * boba_server_cancel -- withdraws a request that is still waiting for
+ * admission: BOBA_OK, after which the library no longer reads or writes its
+ * host buffers and poll never reports it; BOBA_ERR_INVALID_ARG if the id is
+ * unknown or the request has already been admitted (it then completes).
+ * (A serving control; the paper has no counterpart.)
+ */
+boba_status_t boba_server_cancel(boba_server_t *server, int64_t id);
+
 /* boba_server_drain -- blocks until every submitted request has completed. */
 boba_status_t boba_server_drain(boba_server_t *server);
 

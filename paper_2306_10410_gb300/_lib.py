@@ -64,6 +64,7 @@ SIGNATURES = {
     "boba_server_submit": (_I64, [_P, _P, _P, _I64, _I64, _P, _P, _P]),
     "boba_server_poll": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
     "boba_server_drain": (_ST, [_P]),
+    "boba_server_cancel": (_ST, [_P, _I64]),
     "boba_server_stats": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "boba_server_destroy": (None, [_P]),
     "boba_tune_reorder": (_ST, [_P, _P, _I64, _I64, _P, _P, _P, _P, _SZ, ctypes.c_int, _P, _P]),

@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/boba.h"
 
@@ -68,12 +69,16 @@ void merge_path_multiply(int variant, const int64_t *row_ptr, const int32_t *col
 }  // namespace boba
 
 // BOBA_TIMED("name", stream, kernel<<<g, b, smem, stream>>>(args));
+// Every launch also sits in an NVTX range of the same name (header-only NVTX 3;
+// a no-op unless a profiler is attached), so a profiler can filter by phase.
 #define BOBA_TIMED(name, stream, ...)                                  \
     do {                                                               \
         int _slot = -1;                                                \
+        nvtxRangePushA(name);                                          \
         if (::boba::timing_on()) ::boba::timing_begin(name, stream, &_slot); \
         __VA_ARGS__;                                                   \
         if (_slot >= 0) ::boba::timing_end(_slot, stream);             \
+        nvtxRangePop();                                                \
     } while (0)
 
 #define BOBA_CUDA_TRY(expr)                                   \

@@ -404,6 +404,20 @@ int boba_server_poll(boba_server_t *h, int64_t *ids, double *latency_ms, int *st
     return k;
 }
 
+boba_status_t boba_server_cancel(boba_server_t *h, int64_t id)
+{
+    auto *S = reinterpret_cast<Server *>(h);
+    if (!S) return BOBA_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (auto it = S->pending.begin(); it != S->pending.end(); ++it) {
+        if ((*it)->id != id) continue;
+        delete *it;                 // not admitted: nothing of it is on the device
+        S->pending.erase(it);
+        return BOBA_OK;
+    }
+    return BOBA_ERR_INVALID_ARG;    // unknown, or already admitted
+}
+
 boba_status_t boba_server_drain(boba_server_t *h)
 {
     auto *S = reinterpret_cast<Server *>(h);

@@ -59,6 +59,11 @@ class Server:
         k = self.lib.boba_server_poll(self.h, ids, lat, st, cap)
         return [(int(ids[i]), float(lat[i]), int(st[i])) for i in range(max(k, 0))]
 
+    def cancel(self, rid: int) -> bool:
+        """Withdraw a request still waiting for admission; False if it was already
+        admitted (it then completes) or is unknown."""
+        return self.lib.boba_server_cancel(self.h, int(rid)) == 0
+
     def drain(self):
         rc = self.lib.boba_server_drain(self.h)
         if rc != 0:

@@ -76,6 +76,25 @@ def test_budget_limits_residency(serve):
     assert 0 < st["peak_pool_bytes"] <= budget
 
 
+def test_cancel_waiting_requests(serve):
+    """A request still queued can be withdrawn; the rest complete correctly."""
+    pool = serve.request_pool(4, seed=80, m_lo=2e5, m_hi=3e5)
+    with serve.Server(budget_bytes=64 << 20, spmv_iters=2, max_active=2) as srv:
+        ids = []
+        for _ in range(4):
+            for g in pool:
+                ids.append(srv.submit(g["src"], g["dst"], g["n"], g["x"],
+                                      serve._pinned_out(g["n"])))
+        cancelled = {rid for rid in ids[-6:] if srv.cancel(rid)}
+        assert not srv.cancel(10 ** 9)                 # unknown id
+        srv.drain()
+        done = srv.poll()
+    got = {rid for rid, _, st in done if st == 0}
+    assert len(cancelled) > 0
+    assert got == set(ids) - cancelled
+    assert all(st == 0 for _, _, st in done)
+
+
 def test_request_too_large_is_refused(serve):
     import paper_2306_10410_gb300 as b
     pool = serve.request_pool(1, seed=79, m_lo=1e6, m_hi=1e6)
