@@ -15,11 +15,16 @@
 //     clusters (every SM takes part), and the graphs above kKcap vertices all
 //     together, phase by phase, in six grid-wide launches with their keys in
 //     global memory: init, first occurrence, mark, bitmap scan, emit,
-//     relabel.  Each phase maps a chunk or tile to its graph by a binary
-//     search over per-graph tile counts; the two look-back scans are segmented
-//     by letting the first tile of each graph publish its prefix at once.
-//     Measured on GB300, distributed shared memory was slower than L2 for the
-//     random key accesses of large graphs, hence this default.
+//     relabel.  Each phase maps a chunk or tile to its graph through
+//     per-graph tile counts (resuming from the previous chunk's graph, else a
+//     binary search); the two look-back scans are segmented by letting the
+//     first tile of each graph publish its prefix at once.  The
+//     first-occurrence and relabel phases of graphs of up to a few slices of
+//     kKcap vertices can instead run sliced: one CTA per (graph, slice) holds
+//     the slice's keys or labels in shared memory and streams all of the
+//     graph's endpoints (the schedules of batch_slices).  Measured on GB300,
+//     distributed shared memory was slower than L2 for the random key
+//     accesses of large graphs, hence this default.
 //
 // In both modes a graph goes through the steps of the single-graph path: keys =
 // SENT, first occurrence, first-occurrence bitmap, popcount prefix, labels
