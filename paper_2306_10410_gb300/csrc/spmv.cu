@@ -17,6 +17,8 @@
 //   k_mp_partition / k_mp_spmv / k_mp_fixup   the merge-path SpMV (below),
 //                  the tuned choice for skewed graphs; its shapes differ in
 //                  block size, items per thread and shared-memory carve-out.
+#include <atomic>
+
 #include "common.cuh"
 #include "host.hpp"
 
@@ -28,9 +30,7 @@ constexpr int64_t kChunk = 16384;      // entries per chunk of a long row
 constexpr int kChunkBlock = 1024;
 constexpr int kRowsBlock = 256;
 
-constexpr int kMpBlock = 256;
-constexpr int kMpItems = 8;
-constexpr int kMpTile = kMpBlock * kMpItems;       // path items (row ends + nonzeros) per tile
+constexpr int kMpTile = 2048;      // smallest merge-path tile (path items) of any shape
 
 struct SpmvLayout {
     int64_t cap, max_chunks, mp_tiles;
@@ -173,9 +173,9 @@ __global__ void __launch_bounds__(256) k_spmv_gather(const uint32_t *long_count,
 // ---------------------------------------------------------------------------
 // Merge-path SpMV (Merrill and Garland, "Merge-based parallel sparse matrix-
 // vector multiplication", SC 2016), the load balancing of the paper's
-// evaluation (Sec. 3.3 and 5.1): the path of n_rows row ends and nnz nonzeros is cut
-// into tiles of kMpTile items, so every block gets the same work whatever the
-// row lengths.  Sums run in path order within a thread, then a segmented scan
+// evaluation (Sec. 3.3 and 5.1): the path of n_rows row ends and nnz nonzeros is
+// cut into tiles of block x items path items (the shapes of kMpShapes), so
+// every block gets the same work whatever the row lengths.  Sums run in path order within a thread, then a segmented scan
 // over the threads of a tile, then (for rows crossing tiles) the tiles'
 // carries in tile order: deterministic, but the rounding depends on where a
 // row falls relative to the tiles.
@@ -326,7 +326,6 @@ __device__ __forceinline__ void mp_tile(
     }
 }
 
-
 // CARVE only makes separate instances, so that a shared-memory carve-out set
 // for one variant does not apply to the others.
 template <int MB, int MI, int CARVE = 0>
@@ -403,15 +402,21 @@ int merge_path_items(int variant)
 namespace {
 
 // One launch of k_mp_spmv<MB, MI, CARVE>; with a carve-out cap the attribute
-// is set on that instance only.
+// is set on that instance only, once per device.
 template <int MB, int MI, int CARVE>
 void launch_mp(int carve_kb, const int64_t *row_ptr, const int32_t *col, const float *val,
                const float *x, float *y, int64_t n, int64_t nnz, const int2 *part, int32_t *crow,
                float *cval, const uint32_t *skip, int64_t tiles, cudaStream_t stream)
 {
-    if (carve_kb > 0)
+    static std::atomic<uint64_t> done{0};          // devices whose attribute is set
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t bit = 1ull << (dev & 63);
+    if (carve_kb > 0 && (done.load() & bit) == 0) {
         cudaFuncSetAttribute((const void *)k_mp_spmv<MB, MI, CARVE>,
                              cudaFuncAttributePreferredSharedMemoryCarveout, carve_kb * 100 / 228);
+        done.fetch_or(bit);
+    }
     BOBA_TIMED("spmv", stream, k_mp_spmv<MB, MI, CARVE><<<(unsigned)tiles, MB, 0, stream>>>(
                                    row_ptr, col, val, x, y, n, nnz, part, crow, cval, skip));
 }

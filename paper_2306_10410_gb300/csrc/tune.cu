@@ -1,10 +1,13 @@
 // Autotuner: for each kernel family with several correct launch variants
 // (block size and loads in flight of the first-occurrence and relabel
-// streams, the schedule of the batched path, the lanes per row of the SpMV),
-// time every variant on the caller's data, check that it gives the same bits
-// as the default, and keep the fastest for that size class (log2 of the size)
-// on this device.  Choices can be saved to and loaded from a text file keyed
-// by GPU name.
+// streams, the schedule of the batched path, the SpMV kernel and shape --
+// lanes per row, or merge-path block, items and shared-memory carve-out --
+// and the ranking of the radix passes), time every variant on the caller's
+// data and keep the fastest for that size class (log2 of the size) on this
+// device.  Integer results must equal the default's bit for bit (a variant
+// that differs is skipped); the SpMV shapes differ only in the order of fp32
+// sums, each within the error bound.  Choices can be saved to and loaded from
+// a text file keyed by GPU name.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
