@@ -5,10 +5,11 @@
 // A stable LSD radix sort of (key = dst, value = src) with 8-bit digits:
 //   k_csr_hist      per-digit histograms of all passes in one read of dst
 //   k_csr_digits    exclusive scan of each pass's 256 digit counts
-//   k_csr_pass      one pass: stable in-tile ranking (warp match + per-warp
-//                   digit counters, items striped so processing order is input
-//                   order), per-digit decoupled look-back across tiles, and a
-//                   scatter staged through shared memory so that runs of equal
+//   k_csr_pass      one pass: stable in-tile ranking (eight bit-ballots, or
+//                   one warp match, + per-warp digit counters, items striped
+//                   so processing order is input order), per-digit decoupled
+//                   look-back across tiles, and a scatter staged through
+//                   shared memory so that runs of equal
 //                   digits are written contiguously (Adinets and Merrill,
 //                   "Onesweep", 2022, for the single-pass scheme); the first
 //                   pass also counts outdeg(u) over the sources it carries
@@ -25,6 +26,8 @@ namespace {
 
 constexpr int kPassBlock = 512;
 constexpr int kPassItems = 8;                        // per thread
+// The NBR sorts and boba_sort_by_dst use the pass shape the CSR tuner picks on
+// R-MAT 24: ballot ranking with registers capped for three blocks per SM.
 constexpr int kPassTile = kPassBlock * kPassItems;  // 4096 items
 constexpr int kMaxPasses = 4;                        // 32-bit keys
 constexpr int kNumCtr = 16;
@@ -118,7 +121,7 @@ __global__ void __launch_bounds__(256) k_csr_digits(const uint32_t *__restrict__
 // One stable LSD pass over digit p (bits 8p .. 8p+7).  BLOCK threads hold
 // ITEMS items each; the first 256 threads also own one digit each for the
 // cross-tile look-back.
-template <int BLOCK, int ITEMS, bool BALLOT = false, int MINB = 1>
+template <int BLOCK, int ITEMS, bool BALLOT = false, int MINB = 2>
 __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t m, int p, const uint32_t *__restrict__ dstart,
@@ -560,7 +563,7 @@ extern "C" boba_status_t boba_nbr(const int64_t *row_ptr, const int32_t *col, in
     for (int p = 0; p < L.passes; ++p) {
         uint32_t *ko = (p & 1) ? U(L.kB) : U(L.kA), *vo = (p & 1) ? U(L.vB) : U(L.vA);
         BOBA_TIMED("nbr", stream,
-                   k_csr_pass<kPassBlock, kPassItems><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
+                   k_csr_pass<kPassBlock, kPassItems, true, 3><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
                        kin, vin, ko, vo, nnz, p, U(L.dst1), lb, U(L.counters), dev->status, p, 0));
         kin = ko;
         vin = vo;
@@ -580,7 +583,7 @@ extern "C" boba_status_t boba_nbr(const int64_t *row_ptr, const int32_t *col, in
     for (int p = 0; p < L.passes; ++p) {
         uint32_t *ko = (p & 1) ? rbuf : fb[0], *vo = (p & 1) ? cbuf : fb[1];
         BOBA_TIMED("nbr", stream,
-                   k_csr_pass<kPassBlock, kPassItems><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
+                   k_csr_pass<kPassBlock, kPassItems, true, 3><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
                        kin, vin, ko, vo, nnz, p, U(L.dst2), lb, U(L.counters), dev->status, p, 0));
         kin = ko;
         vin = vo;
@@ -687,7 +690,7 @@ extern "C" boba_status_t boba_sort_by_dst(const int32_t *src, const int32_t *dst
         uint32_t *ko = last ? reinterpret_cast<uint32_t *>(dst_out) : ((p & 1) ? U(L.kB) : U(L.kA));
         uint32_t *vo = last ? reinterpret_cast<uint32_t *>(src_out) : ((p & 1) ? U(L.vB) : U(L.vA));
         BOBA_TIMED("sort", stream,
-                   k_csr_pass<kPassBlock, kPassItems><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
+                   k_csr_pass<kPassBlock, kPassItems, true, 3><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
                        kin, vin, ko, vo, m, p, U(L.dstart), reinterpret_cast<uint64_t *>(b + L.status),
                        U(L.counters), dev->status, d, base));
         kin = ko;
@@ -765,8 +768,8 @@ extern "C" boba_status_t boba_coo_to_csr(const int32_t *src, const int32_t *dst,
         float *val_p = fuse ? val_out : nullptr;
         const uint32_t *od_in = fuse ? outdeg : nullptr;
         const int tv = tuned_variant(kTuneCsr, m);
-        // 0: match ranking; 1: ballot ranking; 2: ballot ranking with registers
-        // capped for three resident blocks per SM
+        // 0 (default): ballot ranking with registers capped for three resident
+        // blocks per SM; 1: ballot ranking, two blocks; 2: match ranking
         if (tv == 1)
             BOBA_TIMED("csr.pass", stream,
                        k_csr_pass<kPassBlock, kPassItems, true><<<(unsigned)L.tiles, kPassBlock, 0,
@@ -775,13 +778,13 @@ extern "C" boba_status_t boba_coo_to_csr(const int32_t *src, const int32_t *dst,
                            od_in, val_p, ends_p));
         else if (tv == 2)
             BOBA_TIMED("csr.pass", stream,
-                       k_csr_pass<kPassBlock, kPassItems, true, 3><<<(unsigned)L.tiles, kPassBlock,
-                                                                    0, stream>>>(
+                       k_csr_pass<kPassBlock, kPassItems><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
                            kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status, p, 0, od, nn,
                            od_in, val_p, ends_p));
         else
             BOBA_TIMED("csr.pass", stream,
-                       k_csr_pass<kPassBlock, kPassItems><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
+                       k_csr_pass<kPassBlock, kPassItems, true, 3><<<(unsigned)L.tiles, kPassBlock,
+                                                                    0, stream>>>(
                            kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status, p, 0, od, nn,
                            od_in, val_p, ends_p));
         kin = ko;
