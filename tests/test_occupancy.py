@@ -1,0 +1,68 @@
+"""Register budgets of the hot kernels, from `nvcc -Xptxas -v` (no GPU needed).
+
+An unnoticed rise in registers lowers the number of resident blocks and costs
+time without changing any result; these budgets are the ones the measured
+occupancy relies on.
+"""
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2306_10410_gb300 import build as B
+
+
+def ptxas_report(src):
+    """{kernel name fragment: (registers, spill bytes)} for one translation unit."""
+    try:
+        cc = B.nvcc()
+    except Exception:
+        pytest.skip("nvcc not available")
+    with tempfile.TemporaryDirectory() as d:
+        cmd = [cc, *B.ARCH, *B.NVCC_FLAGS, "-Xptxas", "-v", "-c", os.path.join(B.CSRC, src), "-o",
+               os.path.join(d, "x.o")]
+        out = subprocess.run(cmd, capture_output=True, text=True, check=True).stderr
+    rep, name = {}, None
+    for line in out.splitlines():
+        m = re.search(r"Compiling entry function '([^']+)'", line)
+        if m:
+            name = m.group(1)
+            continue
+        m = re.search(r"(\d+) bytes spill stores", line)
+        if m and name:
+            rep.setdefault(name, [0, 0])[1] = int(m.group(1))
+        m = re.search(r"Used (\d+) registers", line)
+        if m and name:
+            rep.setdefault(name, [0, 0])[0] = int(m.group(1))
+    return rep
+
+
+def pick(rep, *frags):
+    return {k: v for k, v in rep.items() if all(f in k for f in frags)}
+
+
+def test_radix_pass_register_budgets():
+    rep = ptxas_report("csr.cu")
+    passes = pick(rep, "k_csr_pass")
+    assert passes, "no radix pass kernels found"
+    for name, (regs, spill) in passes.items():
+        three = "Li3E" in name                      # capped for three blocks of 512 per SM
+        assert regs <= (40 if three else 64), (name, regs)
+        if not three:
+            assert spill <= 8, (name, spill)
+
+
+def test_spmv_and_reorder_register_budgets():
+    rep = ptxas_report("spmv.cu")
+    mp = pick(rep, "k_mp_spmv")
+    assert mp
+    for name, (regs, spill) in mp.items():
+        assert regs <= 48 and spill == 0, (name, regs, spill)
+    rep = ptxas_report("reorder.cu")
+    for frag in ("k_first_v", "k_relabel_v"):
+        ks = pick(rep, frag, "Li512E")            # the 512-thread shapes the tuner picks
+        assert ks
+        for name, (regs, spill) in ks.items():
+            assert regs <= 64 and spill == 0, (name, regs, spill)
