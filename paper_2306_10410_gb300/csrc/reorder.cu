@@ -252,40 +252,67 @@ __global__ void __launch_bounds__(kEmitBlock) k_emit(const uint32_t *__restrict_
     if (threadIdx.x == 0) s_tile = atomicAdd(&counters[kCtrEmitTicket], 1u);
     __syncthreads();
     const int64_t tile = s_tile;
+    // row q of the tile is vertices tile*T + q*4*kEmitBlock .. + 4*kEmitBlock - 1
+    // and thread t holds its vertices 4t .. 4t+3: the int4 key loads of a row
+    // are coalesced, and vertex order is row-major, thread order in a row
     const int64_t v0 = tile * kEmitTileVerts + 4 * (int64_t)threadIdx.x;
-    uint4 k4 = make_uint4(kSent, kSent, kSent, kSent);
-    if (v0 < (int64_t)n) k4 = *reinterpret_cast<const uint4 *>(key + v0);   // key padded to 4
-    const uint32_t kk[4] = {k4.x, k4.y, k4.z, k4.w};
-    uint32_t iso[4], c = 0;
+    constexpr int64_t kRow = 4 * (int64_t)kEmitBlock;
+    uint32_t kk[kEmitGroups][4], cq[kEmitGroups];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        iso[j] = (v0 + j < (int64_t)n && kk[j] == kSent) ? 1u : 0u;
-        c += iso[j];
+    for (int q = 0; q < kEmitGroups; ++q) {
+        const int64_t vq = v0 + q * kRow;
+        uint4 k4 = make_uint4(kSent, kSent, kSent, kSent);
+        if (vq < (int64_t)n) k4 = *reinterpret_cast<const uint4 *>(key + vq);   // key padded to 4
+        kk[q][0] = k4.x;
+        kk[q][1] = k4.y;
+        kk[q][2] = k4.z;
+        kk[q][3] = k4.w;
+        cq[q] = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cq[q] += (vq + j < (int64_t)n && kk[q][j] == kSent) ? 1u : 0u;
     }
-    uint32_t tot;
-    const uint32_t ex = BlockScan<kEmitBlock>::exclusive(c, &tot, sm);
+    // vertices on no edge: offset of each row piece inside the tile
+    __shared__ uint32_t s_rowtot[kEmitGroups];
+    uint32_t within[kEmitGroups];
+#pragma unroll
+    for (int q = 0; q < kEmitGroups; ++q) {
+        uint32_t rt;
+        within[q] = BlockScan<kEmitBlock>::exclusive(cq[q], &rt, sm);
+        if (threadIdx.x == 0) s_rowtot[q] = rt;
+        __syncthreads();                   // the scan's shared words are reused
+    }
+    uint32_t row_before[kEmitGroups], tot = 0;
+#pragma unroll
+    for (int q = 0; q < kEmitGroups; ++q) {
+        row_before[q] = tot + within[q];
+        tot += s_rowtot[q];
+    }
     if (threadIdx.x < 32) {
         const uint64_t p = lookback_exclusive(tstat, tile, tot, status);
         if (threadIdx.x == 0) s_prefix = p;
     }
     __syncthreads();
     const uint32_t on_edges = counters[kCtrTotal];
-    uint32_t next_iso = on_edges + (uint32_t)s_prefix + ex;
-    int32_t lab[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        if (v0 + j >= (int64_t)n) { lab[j] = -1; continue; }
-        if (kk[j] == kSent) lab[j] = (int32_t)(next_iso++);
-        else lab[j] = (int32_t)rank_of_key(kk[j], bitmap, grp);
-        if ((uint32_t)lab[j] < n) perm[lab[j]] = (int32_t)(v0 + j);
-        else raise_status(status, BOBA_ERR_TIMEOUT);   // only after a failed look-back
-    }
-    if (label_vec && v0 + 3 < (int64_t)n) {
-        *reinterpret_cast<int4 *>(label + v0) = make_int4(lab[0], lab[1], lab[2], lab[3]);
-    } else {
+    for (int q = 0; q < kEmitGroups; ++q) {
+        const int64_t vq = v0 + q * kRow;
+        uint32_t next_iso = on_edges + (uint32_t)s_prefix + row_before[q];
+        int32_t lab[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (v0 + j < (int64_t)n) label[v0 + j] = lab[j];
+        for (int j = 0; j < 4; ++j) {
+            if (vq + j >= (int64_t)n) { lab[j] = -1; continue; }
+            if (kk[q][j] == kSent) lab[j] = (int32_t)(next_iso++);
+            else lab[j] = (int32_t)rank_of_key(kk[q][j], bitmap, grp);
+            if ((uint32_t)lab[j] < n) perm[lab[j]] = (int32_t)(vq + j);
+            else raise_status(status, BOBA_ERR_TIMEOUT);   // only after a failed look-back
+        }
+        if (label_vec && vq + 3 < (int64_t)n) {
+            *reinterpret_cast<int4 *>(label + vq) = make_int4(lab[0], lab[1], lab[2], lab[3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (vq + j < (int64_t)n) label[vq + j] = lab[j];
+        }
     }
 }
 

@@ -14,7 +14,8 @@ constexpr int kRelabelUnroll = 4;
 constexpr int kScanBlock = 256;
 constexpr int kScanTileWords = kScanBlock * 8;     // 8 bitmap words (one 32-byte sector) per thread
 constexpr int kEmitBlock = 256;
-constexpr int kEmitTileVerts = kEmitBlock * 4;     // 4 vertices (one int4 of keys) per thread
+constexpr int kEmitGroups = 4;                      // int4 groups of keys per thread
+constexpr int kEmitTileVerts = kEmitBlock * 4 * kEmitGroups;   // 16 vertices per thread
 constexpr int kNumCounters = 8;                    // tickets and totals in the workspace
 constexpr int kCtrScanTicket = 0, kCtrEmitTicket = 1, kCtrTotal = 2;
 
