@@ -214,24 +214,43 @@ __global__ void __launch_bounds__(kScanBlock) k_scan(const uint32_t *__restrict_
     __shared__ typename BlockScan<kScanBlock>::Smem sm;
     __shared__ uint32_t s_tile;
     __shared__ uint64_t s_prefix;
+    __shared__ uint32_t s_rowtot[kScanRows];
     if (threadIdx.x == 0) s_tile = atomicAdd(&counters[kCtrScanTicket], 1u);
     __syncthreads();
     const int64_t tile = s_tile;
-    const uint4 *w = reinterpret_cast<const uint4 *>(bitmap) + (tile * kScanTileWords) / 4 +
-                     2 * threadIdx.x;
-    const uint4 a = w[0], b = w[1];
-    const uint32_t c = __popc(a.x) + __popc(a.y) + __popc(a.z) + __popc(a.w) + __popc(b.x) +
-                       __popc(b.y) + __popc(b.z) + __popc(b.w);
-    uint32_t tot;
-    const uint32_t ex = BlockScan<kScanBlock>::exclusive(c, &tot, sm);
+    // row q of the tile: words tile*T + q*8*kScanBlock .., thread t's sector at 8t
+    constexpr int64_t kRowWords = 8 * (int64_t)kScanBlock;
+    uint32_t within[kScanRows];
+#pragma unroll
+    for (int q = 0; q < kScanRows; ++q) {
+        const uint4 *w = reinterpret_cast<const uint4 *>(bitmap + tile * kScanTileWords +
+                                                         q * kRowWords) + 2 * threadIdx.x;
+        const uint4 a = w[0], b = w[1];
+        const uint32_t c = __popc(a.x) + __popc(a.y) + __popc(a.z) + __popc(a.w) + __popc(b.x) +
+                           __popc(b.y) + __popc(b.z) + __popc(b.w);
+        uint32_t rt;
+        within[q] = BlockScan<kScanBlock>::exclusive(c, &rt, sm);
+        if (threadIdx.x == 0) s_rowtot[q] = rt;
+        __syncthreads();                   // the scan's shared words are reused
+    }
+    uint32_t row_before[kScanRows], tot = 0;
+#pragma unroll
+    for (int q = 0; q < kScanRows; ++q) {
+        row_before[q] = tot + within[q];
+        tot += s_rowtot[q];
+    }
     if (threadIdx.x < 32) {
         const uint64_t p = lookback_exclusive(tstat, tile, tot, status);
         if (threadIdx.x == 0) s_prefix = p;
     }
     __syncthreads();
-    grp[tile * kScanBlock + threadIdx.x] = (uint32_t)(s_prefix + ex);
+#pragma unroll
+    for (int q = 0; q < kScanRows; ++q)
+        grp[(tile * kScanTileWords + q * kRowWords) / 8 + threadIdx.x] =
+            (uint32_t)(s_prefix + row_before[q]);
     if (tile == tiles - 1 && threadIdx.x == 0) counters[kCtrTotal] = (uint32_t)(s_prefix + tot);
 }
+
 
 // ---------------------------------------------------------------------------
 // k_emit: ParMapKeys (Alg. 2): label[v] = rank of key[v]; a vertex on no edge

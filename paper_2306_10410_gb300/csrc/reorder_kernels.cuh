@@ -12,7 +12,8 @@ constexpr int kFirstUnroll = 4;         // int4 loads in flight per thread
 constexpr int kRelabelBlock = 256;
 constexpr int kRelabelUnroll = 4;
 constexpr int kScanBlock = 256;
-constexpr int kScanTileWords = kScanBlock * 8;     // 8 bitmap words (one 32-byte sector) per thread
+constexpr int kScanRows = 4;                        // rows of 8 bitmap words per thread
+constexpr int kScanTileWords = kScanBlock * 8 * kScanRows;   // a thread: one 32-byte sector per row
 constexpr int kEmitBlock = 256;
 constexpr int kEmitGroups = 4;                      // int4 groups of keys per thread
 constexpr int kEmitTileVerts = kEmitBlock * 4 * kEmitGroups;   // 16 vertices per thread
