@@ -41,7 +41,8 @@ __device__ __forceinline__ uint64_t pass_flag(int p, bool inclusive)
 }
 constexpr uint64_t kPassValMask = (1ull << 60) - 1;
 
-constexpr int kRowTile = 1024;                       // vertices per row_ptr scan tile
+constexpr int kRowRows = 4;                          // rows of 4 vertices per thread
+constexpr int kRowTile = 256 * 4 * kRowRows;         // vertices per row_ptr scan tile
 constexpr int kCtrRowTicket = 8;
 
 struct CsrLayout {
@@ -350,25 +351,42 @@ __global__ void __launch_bounds__(256) k_csr_rowptr(const uint32_t *__restrict__
     if (threadIdx.x == 0) s_tile = atomicAdd(&counters[kCtrRowTicket], 1u);
     __syncthreads();
     const int64_t tile = s_tile;
-    const int64_t v0 = tile * kRowTile + 4 * (int64_t)threadIdx.x;
-    const uint4 e = *reinterpret_cast<const uint4 *>(ends + v0);    // padded, zero beyond n
-    uint32_t run[4];
-    run[0] = e.x;
-    run[1] = max(run[0], e.y);
-    run[2] = max(run[1], e.z);
-    run[3] = max(run[2], e.w);
-    uint32_t tot;
-    const uint32_t ex = BlockScan<256, OpMax32>::exclusive(run[3], &tot, sm);
+    // row q of the tile: vertices tile*T + q*1024 .., thread t's four at 4t
+    __shared__ uint32_t s_rowmax[kRowRows];
+    uint32_t run[kRowRows][4], within[kRowRows];
+#pragma unroll
+    for (int q = 0; q < kRowRows; ++q) {
+        const int64_t vq = tile * kRowTile + q * 1024 + 4 * (int64_t)threadIdx.x;
+        const uint4 e = *reinterpret_cast<const uint4 *>(ends + vq);   // padded, zero beyond n
+        run[q][0] = e.x;
+        run[q][1] = max(run[q][0], e.y);
+        run[q][2] = max(run[q][1], e.z);
+        run[q][3] = max(run[q][2], e.w);
+        uint32_t rt;
+        within[q] = BlockScan<256, OpMax32>::exclusive(run[q][3], &rt, sm);
+        if (threadIdx.x == 0) s_rowmax[q] = rt;
+        __syncthreads();                   // the scan's shared words are reused
+    }
+    uint32_t row_before[kRowRows], tot = 0;
+#pragma unroll
+    for (int q = 0; q < kRowRows; ++q) {
+        row_before[q] = max(tot, within[q]);
+        tot = max(tot, s_rowmax[q]);
+    }
     if (threadIdx.x < 32) {
         const uint64_t p = lookback_exclusive<OpMax>(tstat, tile, tot, status);
         if (threadIdx.x == 0) s_prefix = p;
     }
     __syncthreads();
-    const uint32_t pre = max((uint32_t)s_prefix, ex);
     if (tile == 0 && threadIdx.x == 0) row_ptr[0] = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-        if (v0 + j < n) row_ptr[v0 + j + 1] = (int64_t)max(pre, run[j]);
+    for (int q = 0; q < kRowRows; ++q) {
+        const int64_t vq = tile * kRowTile + q * 1024 + 4 * (int64_t)threadIdx.x;
+        const uint32_t pre = max((uint32_t)s_prefix, row_before[q]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (vq + j < n) row_ptr[vq + j + 1] = (int64_t)max(pre, run[q][j]);
+    }
 }
 
 __global__ void k_rowptr_zero(int64_t *row_ptr, int64_t n)
