@@ -59,8 +59,11 @@ constexpr int kMaxSlices = 8;              // sliced large path: n <= kMaxSlices
 // tiles of the phase-batched large-graph path
 constexpr int kLB = 256;                   // threads per block
 constexpr int kPosChunk = kLB * 64;        // positions of I ++ J per block step (4 rounds of 16)
-constexpr int kVtxTile = kLB * 4;          // vertices per tile
-constexpr int kWordTile = kLB * 8;         // bitmap words per scan tile
+constexpr int kBlRows = 4;                 // rows per tile: a thread takes one piece of each
+constexpr int kVtxRow = kLB * 4;           // vertices per row (one int4 of keys per thread)
+constexpr int kWordRow = kLB * 8;          // bitmap words per row (one 32-byte sector per thread)
+constexpr int kVtxTile = kVtxRow * kBlRows;     // vertices per tile
+constexpr int kWordTile = kWordRow * kBlRows;   // bitmap words per scan tile
 constexpr int kEdgeChunk = kLB * 32;       // edges per relabel block step (4 rounds of 8 per thread)
 
 enum BatchMode { kBatchCluster = 0, kBatchSplit = 1 };
@@ -558,12 +561,15 @@ __global__ void __launch_bounds__(kLB) k_bl_mark(BatchArgs a)
         block_find(a, a.lg_vt, c, it, s_it, hint);
         const uint32_t *key = a.kl + (size_t)a.lg_vt[it.j] * kVtxTile;
         uint32_t *bm = a.lbm + (size_t)a.lg_wt[it.j] * kWordTile;
-        const int64_t v0 = (int64_t)it.local * kVtxTile + 4 * threadIdx.x;
-        const uint4 k4 = *reinterpret_cast<const uint4 *>(key + v0);
-        const uint32_t kk[4] = {k4.x, k4.y, k4.z, k4.w};
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (v0 + q < it.n && kk[q] != kSent) atomicOr(&bm[kk[q] >> 5], 1u << (kk[q] & 31u));
+        for (int r = 0; r < kBlRows; ++r) {
+            const int64_t v0 = (int64_t)it.local * kVtxTile + r * kVtxRow + 4 * threadIdx.x;
+            const uint4 k4 = *reinterpret_cast<const uint4 *>(key + v0);
+            const uint32_t kk[4] = {k4.x, k4.y, k4.z, k4.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (v0 + q < it.n && kk[q] != kSent) atomicOr(&bm[kk[q] >> 5], 1u << (kk[q] & 31u));
+        }
     }
 }
 
@@ -572,6 +578,7 @@ __global__ void __launch_bounds__(kLB) k_bl_scan(BatchArgs a)
     __shared__ LargeItem s_it;
     uint32_t hint = 0;                     // thread 0: graph of the previous item
     __shared__ typename BlockScan<kLB>::Smem sm;
+    __shared__ uint32_t s_rowtot[kBlRows];
     __shared__ uint32_t s_tile;
     __shared__ uint64_t s_pre;
     const uint32_t L = a.hdr[kHdrLarge];
@@ -584,19 +591,35 @@ __global__ void __launch_bounds__(kLB) k_bl_scan(BatchArgs a)
         if (t >= total) break;
         LargeItem it;
         block_find(a, a.lg_wt, t, it, s_it, hint);
-        const size_t w0 = (size_t)t * kWordTile + 8 * threadIdx.x;
-        const uint4 x0 = __ldcg(reinterpret_cast<const uint4 *>(a.lbm + w0));
-        const uint4 x1 = __ldcg(reinterpret_cast<const uint4 *>(a.lbm + w0) + 1);
-        const uint32_t c = __popc(x0.x) + __popc(x0.y) + __popc(x0.z) + __popc(x0.w) +
-                           __popc(x1.x) + __popc(x1.y) + __popc(x1.z) + __popc(x1.w);
-        uint32_t tot;
-        const uint32_t ex = BlockScan<kLB>::exclusive(c, &tot, sm);
+        // row r of the tile: words t*kWordTile + r*kWordRow .., this thread's sector at 8*tid
+        uint32_t within[kBlRows];
+#pragma unroll
+        for (int r = 0; r < kBlRows; ++r) {
+            const size_t w0 = (size_t)t * kWordTile + r * kWordRow + 8 * threadIdx.x;
+            const uint4 x0 = __ldcg(reinterpret_cast<const uint4 *>(a.lbm + w0));
+            const uint4 x1 = __ldcg(reinterpret_cast<const uint4 *>(a.lbm + w0) + 1);
+            const uint32_t c = __popc(x0.x) + __popc(x0.y) + __popc(x0.z) + __popc(x0.w) +
+                               __popc(x1.x) + __popc(x1.y) + __popc(x1.z) + __popc(x1.w);
+            uint32_t rt;
+            within[r] = BlockScan<kLB>::exclusive(c, &rt, sm);
+            if (threadIdx.x == 0) s_rowtot[r] = rt;
+            __syncthreads();               // the scan's shared words are reused
+        }
+        uint32_t before[kBlRows], tot = 0;
+#pragma unroll
+        for (int r = 0; r < kBlRows; ++r) {
+            before[r] = tot + within[r];
+            tot += s_rowtot[r];
+        }
         if (threadIdx.x < 32) {
             const uint64_t p = lookback_exclusive(a.lts_scan, t, tot, a.status, it.local == 0);
             if (threadIdx.x == 0) s_pre = p;
         }
         __syncthreads();
-        a.lgrp[w0 >> 3] = (uint32_t)s_pre + ex;
+#pragma unroll
+        for (int r = 0; r < kBlRows; ++r)
+            a.lgrp[((size_t)t * kWordTile + r * kWordRow + 8 * threadIdx.x) >> 3] =
+                (uint32_t)s_pre + before[r];
         if (threadIdx.x == 0 && t + 1 == a.lg_wt[it.j + 1]) a.lg_tot[it.j] = (uint32_t)s_pre + tot;
         __syncthreads();
     }
@@ -607,6 +630,7 @@ __global__ void __launch_bounds__(kLB) k_bl_emit(BatchArgs a)
     __shared__ LargeItem s_it;
     uint32_t hint = 0;                     // thread 0: graph of the previous item
     __shared__ typename BlockScan<kLB>::Smem sm;
+    __shared__ uint32_t s_rowtot[kBlRows];
     __shared__ uint32_t s_tile;
     __shared__ uint64_t s_pre;
     const uint32_t L = a.hdr[kHdrLarge];
@@ -621,47 +645,68 @@ __global__ void __launch_bounds__(kLB) k_bl_emit(BatchArgs a)
         block_find(a, a.lg_vt, t, it, s_it, hint);
         uint32_t *key = a.kl + (size_t)a.lg_vt[it.j] * kVtxTile;
         const size_t wbase = (size_t)a.lg_wt[it.j] * kWordTile;
-        const int64_t v0 = (int64_t)it.local * kVtxTile + 4 * threadIdx.x;
-        const uint4 k4 = *reinterpret_cast<const uint4 *>(key + v0);
-        const uint32_t kk[4] = {k4.x, k4.y, k4.z, k4.w};
-        uint32_t c = 0;
+        // row r of the tile: vertices local*kVtxTile + r*kVtxRow .., this
+        // thread's four at 4*tid; vertex order is row-major
+        uint32_t kk[kBlRows][4], within[kBlRows];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) c += (v0 + q < it.n && kk[q] == kSent) ? 1u : 0u;
-        uint32_t tot;
-        const uint32_t ex = BlockScan<kLB>::exclusive(c, &tot, sm);
+        for (int r = 0; r < kBlRows; ++r) {
+            const int64_t v0 = (int64_t)it.local * kVtxTile + r * kVtxRow + 4 * threadIdx.x;
+            const uint4 k4 = *reinterpret_cast<const uint4 *>(key + v0);
+            kk[r][0] = k4.x;
+            kk[r][1] = k4.y;
+            kk[r][2] = k4.z;
+            kk[r][3] = k4.w;
+            uint32_t c = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) c += (v0 + q < it.n && kk[r][q] == kSent) ? 1u : 0u;
+            uint32_t rt;
+            within[r] = BlockScan<kLB>::exclusive(c, &rt, sm);
+            if (threadIdx.x == 0) s_rowtot[r] = rt;
+            __syncthreads();               // the scan's shared words are reused
+        }
+        uint32_t before[kBlRows], tot = 0;
+#pragma unroll
+        for (int r = 0; r < kBlRows; ++r) {
+            before[r] = tot + within[r];
+            tot += s_rowtot[r];
+        }
         if (threadIdx.x < 32) {
             const uint64_t p = lookback_exclusive(a.lts_emit, t, tot, a.status, it.local == 0);
             if (threadIdx.x == 0) s_pre = p;
         }
         __syncthreads();
         const uint32_t K = __ldcg(a.lg_tot + it.j);
-        uint32_t next_iso = K + (uint32_t)s_pre + ex;
-        uint32_t lab[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            lab[q] = kSent;
-            if (v0 + q >= it.n) continue;
-            if (kk[q] == kSent) {
-                lab[q] = next_iso++;
-            } else {
-                const uint32_t k = kk[q];
-                const size_t gidx = (wbase >> 3) + (k >> 8);
-                const uint4 *gw = reinterpret_cast<const uint4 *>(a.lbm + (gidx << 3));
-                const uint4 q0 = __ldcg(gw), q1 = __ldcg(gw + 1);
-                const uint32_t ws[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-                const uint32_t wi = (k >> 5) & 7u;
-                uint32_t r = __ldcg(a.lgrp + gidx);      // prefixes restart at each graph
+        for (int r = 0; r < kBlRows; ++r) {
+            const int64_t v0 = (int64_t)it.local * kVtxTile + r * kVtxRow + 4 * threadIdx.x;
+            uint32_t next_iso = K + (uint32_t)s_pre + before[r];
+            uint32_t lab[4];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    if ((uint32_t)i < wi) r += __popc(ws[i]);
-                    else if ((uint32_t)i == wi) r += __popc(ws[i] & ((1u << (k & 31u)) - 1u));
+            for (int q = 0; q < 4; ++q) {
+                lab[q] = kSent;
+                if (v0 + q >= it.n) continue;
+                if (kk[r][q] == kSent) {
+                    lab[q] = next_iso++;
+                } else {
+                    const uint32_t k = kk[r][q];
+                    const size_t gidx = (wbase >> 3) + (k >> 8);
+                    const uint4 *gw = reinterpret_cast<const uint4 *>(a.lbm + (gidx << 3));
+                    const uint4 q0 = __ldcg(gw), q1 = __ldcg(gw + 1);
+                    const uint32_t ws[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+                    const uint32_t wi = (k >> 5) & 7u;
+                    uint32_t rk = __ldcg(a.lgrp + gidx);      // prefixes restart at each graph
+#pragma unroll
+                    for (int i2 = 0; i2 < 8; ++i2) {
+                        if ((uint32_t)i2 < wi) rk += __popc(ws[i2]);
+                        else if ((uint32_t)i2 == wi) rk += __popc(ws[i2] & ((1u << (k & 31u)) - 1u));
+                    }
+                    lab[q] = rk;
                 }
-                lab[q] = r;
+                if (lab[q] < (uint32_t)it.n) a.perm[it.V0 + lab[q]] = (int32_t)(v0 + q);
+                else raise_status(a.status, BOBA_ERR_TIMEOUT);
             }
-            if (lab[q] < (uint32_t)it.n) a.perm[it.V0 + lab[q]] = (int32_t)(v0 + q);
-            else raise_status(a.status, BOBA_ERR_TIMEOUT);
+            *reinterpret_cast<uint4 *>(key + v0) = make_uint4(lab[0], lab[1], lab[2], lab[3]);
         }
-        *reinterpret_cast<uint4 *>(key + v0) = make_uint4(lab[0], lab[1], lab[2], lab[3]);
         __syncthreads();
     }
 }
