@@ -425,6 +425,35 @@ def compare_orders(args, boba, torch, dev, stream, src, dst, so, do, m, n, row_p
         out[name] = {"sort_ms": round(statistics.median(ts), 4),
                      "reorder_ms": round(statistics.median(tr), 4),
                      "csr_plus_spmv_ms": round(statistics.median(tsp), 4), "nbr32": round(v, 5)}
+    # the other readings (Fig. 1 interleaved, Alg. 2's racy store): reorder
+    # time, and the locality and SpMV of the order they give
+    for name, variant in (("boba_interleaved", 1), ("boba_racy", 2)):
+        tr = []
+        for rep in range(4):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            flush.zero_()
+            ev[0].record(stream)
+            boba.check(boba.boba_reorder_variant(src, dst, m, n, perm2, s3, d3, variant, ws_r2,
+                                                 ws_r2.numel(), stream), "variant")
+            ev[1].record(stream)
+            torch.cuda.synchronize(dev)
+            if rep:
+                tr.append(ev[0].elapsed_time(ev[1]))
+        boba.check(boba.boba_coo_to_csr(s3, d3, m, n, row_ptr, col, val, ws_c, ws_c.numel(),
+                                        stream), "csr")
+        ts = []
+        for rep in range(4):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            boba.check(boba.boba_spmv_csr(row_ptr, col, val, x, y, n, m, ws_s, ws_s.numel(),
+                                          stream), "spmv")
+            ev[1].record(stream)
+            torch.cuda.synchronize(dev)
+            if rep:
+                ts.append(ev[0].elapsed_time(ev[1]))
+        v, _ = boba.nbr(row_ptr, col, ids_per_line=32)
+        out[name] = {"reorder_ms": round(statistics.median(tr), 4),
+                     "spmv_ms": round(statistics.median(ts), 4), "nbr32": round(v, 5)}
     del s2, d2, s3, d3, ws_sort, ws_r2
     boba.stream_status(stream)
     # NBR spatial-locality metric (Sec. 5.2) of the two CSRs, lines of 32 IDs, and
