@@ -522,9 +522,13 @@ boba_status_t boba_tune_spmv(const int64_t *row_ptr, const int32_t *col, const f
                              size_t ws_bytes, int reps, int *chosen, void *stream);
 
 /*
- * boba_tune_csr -- the same for the in-tile ranking of boba_coo_to_csr's radix
- * passes (variant 0: warp match instruction; 1: eight bit ballots), keyed by
- * m; every variant's CSR must equal the default's bit for bit.
+ * boba_tune_csr -- the same for the radix passes of boba_coo_to_csr: their
+ * in-tile ranking and tile shape (variant 0: 512 threads x 8 keys, eight
+ * bit-ballots, registers capped for three blocks per SM; 1: the same with two
+ * blocks; 2: one warp match instruction; 3: per-warp shared-memory OR masks of
+ * the lanes holding each digit; 4 and 5: ballots and OR masks in 256 x 16
+ * tiles; 6: ballots in 384 x 16 tiles; 7: ballots in 512 x 16 tiles), keyed
+ * by m; every variant's CSR must equal the default's bit for bit.
  */
 boba_status_t boba_tune_csr(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
                             int64_t *row_ptr, int32_t *col_out, float *val_out, void *ws,

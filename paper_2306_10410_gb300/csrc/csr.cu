@@ -5,9 +5,11 @@
 // A stable LSD radix sort of (key = dst, value = src) with 8-bit digits:
 //   k_csr_hist      per-digit histograms of all passes in one read of dst
 //   k_csr_digits    exclusive scan of each pass's 256 digit counts
-//   k_csr_pass      one pass: stable in-tile ranking (eight bit-ballots, or
-//                   one warp match, + per-warp digit counters, items striped
-//                   so processing order is input order), per-digit decoupled
+//   k_csr_pass      one pass: stable in-tile ranking (eight bit-ballots, one
+//                   warp match, or per-warp shared-memory OR masks of the
+//                   lanes holding each digit, + per-warp digit counters,
+//                   items striped so processing order is input order),
+//                   per-digit decoupled
 //                   look-back across tiles, and a scatter staged through
 //                   shared memory so that runs of equal
 //                   digits are written contiguously (Adinets and Merrill,
@@ -18,6 +20,8 @@
 //                   last pass does this itself as it writes its output
 //   k_csr_rowptr    row_ptr[v+1] = max over u <= v of ends[u] (a single-pass
 //                   max-scan with decoupled look-back), row_ptr[0] = 0
+#include <atomic>
+
 #include "common.cuh"
 #include "host.hpp"
 
@@ -30,6 +34,10 @@ constexpr int kPassItems = 8;                        // per thread
 // R-MAT 24: ballot ranking with registers capped for three blocks per SM.
 constexpr int kPassTile = kPassBlock * kPassItems;  // 4096 items
 constexpr int kMaxPasses = 4;                        // 32-bit keys
+// How a warp finds the lanes that share its digit: one match instruction,
+// eight bit-ballots intersected, or each lane ORs its bit into a per-warp
+// shared-memory mask of its digit and reads the mask back.
+constexpr int kRankMatch = 0, kRankBallot = 1, kRankOr = 2;
 constexpr int kNumCtr = 16;
 
 // Look-back status of (tile, digit) for pass p, one u64: the top 4 bits hold
@@ -122,7 +130,7 @@ __global__ void __launch_bounds__(256) k_csr_digits(const uint32_t *__restrict__
 // One stable LSD pass over digit p (bits 8p .. 8p+7).  BLOCK threads hold
 // ITEMS items each; the first 256 threads also own one digit each for the
 // cross-tile look-back.
-template <int BLOCK, int ITEMS, bool BALLOT = false, int MINB = 2>
+template <int BLOCK, int ITEMS, int RANK = kRankMatch, int MINB = 2>
 __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t m, int p, const uint32_t *__restrict__ dstart,
@@ -134,31 +142,41 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
     constexpr int WARPS = BLOCK / 32;
     constexpr int WARP_ITEMS = 32 * ITEMS;
     static_assert(BLOCK >= 256, "one thread per digit");
-    __shared__ uint32_t s_keys[TILE];
-    __shared__ uint32_t s_vals[TILE];
+    // the staged tile (TILE keys, then TILE values) in dynamic shared memory
+    extern __shared__ __align__(16) uint32_t s_stage[];
+    uint32_t *const s_keys = s_stage;
+    uint32_t *const s_vals = s_stage + TILE;
     __shared__ uint16_t s_wcnt[WARPS][256];      // per-warp digit counts, then warp prefixes
     __shared__ uint32_t s_tpre[256];              // tile-local exclusive digit offsets
     __shared__ uint32_t s_base[256];              // global start of this tile's run of digit d
+    constexpr int NBIN = RANK == kRankOr ? 257 : 1;   // digits and the invalid tail
+    __shared__ uint32_t s_bins[RANK == kRankOr ? WARPS : 1][NBIN];
     __shared__ typename BlockScan<BLOCK>::Smem sm;
     __shared__ uint32_t s_tile;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_tile = atomicAdd(&counters[p], 1u);
     for (int i = threadIdx.x; i < WARPS * 256; i += BLOCK) (&s_wcnt[0][0])[i] = 0;
+    if constexpr (RANK == kRankOr)
+        for (int i = threadIdx.x; i < WARPS * NBIN; i += BLOCK) (&s_bins[0][0])[i] = 0;
     __syncthreads();
     const int64_t tile = s_tile;
     const int64_t t0 = tile * TILE;
     const int shift = base_shift + 8 * digit;
+    // items of this tile; tile-local indices and global positions fit 32 bits
+    // (m < 2^31)
+    const int valid_n = (m - t0) < TILE ? (int)(m - t0) : TILE;
+    const uint32_t *kin_t = kin + t0, *vin_t = vin + t0;
 
     // load: item (warp, k, lane) is tile index warp*WARP_ITEMS + k*32 + lane, so
     // the k-major / lane-minor processing order of a warp is the input order
     uint32_t key[ITEMS], val[ITEMS], rank[ITEMS];
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
-        const int64_t i = t0 + warp * WARP_ITEMS + k * 32 + lane;
-        if (i < m) {
-            key[k] = __ldcs(kin + i);
-            val[k] = __ldcs(vin + i);
+        const int j = warp * WARP_ITEMS + k * 32 + lane;
+        if (j < valid_n) {
+            key[k] = __ldcs(kin_t + j);
+            val[k] = __ldcs(vin_t + j);
         } else {
             key[k] = 0xFFFFFFFFu;
             val[k] = 0;
@@ -169,8 +187,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
         // values (the sources): fire-and-forget L2 reductions beside the ranking
 #pragma unroll
         for (int k = 0; k < ITEMS; ++k) {
-            const int64_t i = t0 + warp * WARP_ITEMS + k * 32 + lane;
-            if (i < m) {
+            if (warp * WARP_ITEMS + k * 32 + lane < valid_n) {
                 if (val[k] < n) atomicAdd(&outdeg[val[k]], 1u);
                 else raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE);
             }
@@ -179,11 +196,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
     const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
-        const int64_t i = t0 + warp * WARP_ITEMS + k * 32 + lane;
-        const bool valid = i < m;
+        const bool valid = warp * WARP_ITEMS + k * 32 + lane < valid_n;
         const uint32_t d = valid ? ((key[k] >> shift) & 255u) : 256u;
         unsigned peers;
-        if constexpr (BALLOT) {
+        if constexpr (RANK == kRankOr) {
+            atomicOr(&s_bins[warp][d], 1u << lane);
+            __syncwarp();
+            peers = s_bins[warp][d];
+        } else if constexpr (RANK == kRankBallot) {
             // lanes with the same digit: intersect 8 bit-ballots (and the
             // valid/invalid split) instead of one match instruction
             const unsigned vm = __ballot_sync(kFull, valid);
@@ -205,6 +225,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
         old = __shfl_sync(kFull, old, leader);
         rank[k] = old + __popc(peers & lt);
         __syncwarp();
+        if constexpr (RANK == kRankOr) {
+            // every lane has read its mask: the group's first lane clears it
+            // for the next round
+            if (lane == leader) s_bins[warp][d] = 0;
+            __syncwarp();
+        }
     }
     __syncthreads();
     // digit d = threadIdx.x (< 256): tile count, warp prefixes, tile-local offsets
@@ -270,8 +296,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
     // stage the tile in shared memory in sorted order
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
-        const int64_t i = t0 + warp * WARP_ITEMS + k * 32 + lane;
-        if (i < m) {
+        if (warp * WARP_ITEMS + k * 32 + lane < valid_n) {
             const uint32_t dd = (key[k] >> shift) & 255u;
             const uint32_t pos = s_tpre[dd] + s_wcnt[warp][dd] + rank[k];
             s_keys[pos] = key[k];
@@ -280,7 +305,6 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
     }
     __syncthreads();
     // write out: consecutive threads write consecutive slots of a digit run
-    const int64_t valid_n = (m - t0) < TILE ? (m - t0) : TILE;
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
         const int j = k * BLOCK + threadIdx.x;
@@ -288,7 +312,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
             const uint32_t kk = s_keys[j];
             const uint32_t vv = s_vals[j];
             const uint32_t dd = (kk >> shift) & 255u;
-            const int64_t g = (int64_t)s_base[dd] + (j - (int64_t)s_tpre[dd]);
+            const uint32_t g = s_base[dd] + (uint32_t)(j - (int)s_tpre[dd]);
             __stcs(vout + g, vv);
             if (ends == nullptr) {
                 __stcs(kout + g, kk);
@@ -308,13 +332,56 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
             if (kk < n) {
                 const int run_end = dd < 255u ? (int)s_tpre[dd + 1] : (int)valid_n;
                 if (j + 1 < run_end) {
-                    if (s_keys[j + 1] != kk) ends[kk] = (uint32_t)(g + 1);
+                    if (s_keys[j + 1] != kk) ends[kk] = g + 1;
                 } else {
-                    atomicMax(&ends[kk], (uint32_t)(g + 1));
+                    atomicMax(&ends[kk], g + 1);
                 }
             }
         }
     }
+}
+
+// One radix pass of the CSR build in a given shape (the tuner's variants).
+// Every shape's tile holds at least kPassTile items, so the look-back status
+// array sized for kPassTile tiles serves all of them.
+struct CsrPassArgs {
+    const uint32_t *kin, *vin;
+    uint32_t *kout, *vout;
+    int64_t m;
+    int p;
+    const uint32_t *dstart;
+    uint64_t *lb;
+    uint32_t *ctr, *status, *outdeg;
+    uint32_t n;
+    const uint32_t *outdeg_in;
+    float *val_out;
+    uint32_t *ends;
+    int digit = 0, base_shift = 0;   // key bits base_shift + 8 digit .. + 7; 0, 0: digit p
+};
+
+template <int BLOCK, int ITEMS, int RANK, int MINB>
+void csr_pass_launch(const char *name, const CsrPassArgs &a, cudaStream_t stream)
+{
+    constexpr int TILE = BLOCK * ITEMS;
+    static_assert(TILE >= kPassTile, "the status array is sized for kPassTile tiles");
+    constexpr size_t smem = (size_t)TILE * 8;
+    // static plus dynamic shared memory above 48 KB needs the opt-in, and
+    // several shapes are there (the OR masks alone take 16 KB): set it for
+    // every shape, once per device
+    static std::atomic<uint64_t> done{0};          // devices whose attribute is set
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t bit = 1ull << (dev & 63);
+    if ((done.load() & bit) == 0) {
+        cudaFuncSetAttribute((const void *)k_csr_pass<BLOCK, ITEMS, RANK, MINB>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        done.fetch_or(bit);
+    }
+    const unsigned tiles = (unsigned)cdiv(a.m > 0 ? a.m : 1, TILE);
+    BOBA_TIMED(name, stream,
+               k_csr_pass<BLOCK, ITEMS, RANK, MINB><<<tiles, BLOCK, smem, stream>>>(
+                   a.kin, a.vin, a.kout, a.vout, a.m, a.p, a.dstart, a.lb, a.ctr, a.status,
+                   a.digit, a.base_shift, a.outdeg, a.n, a.outdeg_in, a.val_out, a.ends));
 }
 
 // ends[k] = 1 + index of the last sorted entry with key k (0 if none);
@@ -580,9 +647,10 @@ extern "C" boba_status_t boba_nbr(const int64_t *row_ptr, const int32_t *col, in
     const uint32_t *kin = reinterpret_cast<const uint32_t *>(col), *vin = U(L.rows);
     for (int p = 0; p < L.passes; ++p) {
         uint32_t *ko = (p & 1) ? U(L.kB) : U(L.kA), *vo = (p & 1) ? U(L.vB) : U(L.vA);
-        BOBA_TIMED("nbr", stream,
-                   k_csr_pass<kPassBlock, kPassItems, true, 3><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
-                       kin, vin, ko, vo, nnz, p, U(L.dst1), lb, U(L.counters), dev->status, p, 0));
+        csr_pass_launch<kPassBlock, kPassItems, kRankBallot, 3>(
+            "nbr", CsrPassArgs{kin, vin, ko, vo, nnz, p, U(L.dst1), lb, U(L.counters), dev->status,
+                               nullptr, 0, nullptr, nullptr, nullptr, p, 0},
+            stream);
         kin = ko;
         vin = vo;
     }
@@ -600,9 +668,10 @@ extern "C" boba_status_t boba_nbr(const int64_t *row_ptr, const int32_t *col, in
     vin = cbuf;
     for (int p = 0; p < L.passes; ++p) {
         uint32_t *ko = (p & 1) ? rbuf : fb[0], *vo = (p & 1) ? cbuf : fb[1];
-        BOBA_TIMED("nbr", stream,
-                   k_csr_pass<kPassBlock, kPassItems, true, 3><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
-                       kin, vin, ko, vo, nnz, p, U(L.dst2), lb, U(L.counters), dev->status, p, 0));
+        csr_pass_launch<kPassBlock, kPassItems, kRankBallot, 3>(
+            "nbr", CsrPassArgs{kin, vin, ko, vo, nnz, p, U(L.dst2), lb, U(L.counters), dev->status,
+                               nullptr, 0, nullptr, nullptr, nullptr, p, 0},
+            stream);
         kin = ko;
         vin = vo;
     }
@@ -707,10 +776,11 @@ extern "C" boba_status_t boba_sort_by_dst(const int32_t *src, const int32_t *dst
         const bool last = d == digits - 1;
         uint32_t *ko = last ? reinterpret_cast<uint32_t *>(dst_out) : ((p & 1) ? U(L.kB) : U(L.kA));
         uint32_t *vo = last ? reinterpret_cast<uint32_t *>(src_out) : ((p & 1) ? U(L.vB) : U(L.vA));
-        BOBA_TIMED("sort", stream,
-                   k_csr_pass<kPassBlock, kPassItems, true, 3><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
-                       kin, vin, ko, vo, m, p, U(L.dstart), reinterpret_cast<uint64_t *>(b + L.status),
-                       U(L.counters), dev->status, d, base));
+        csr_pass_launch<kPassBlock, kPassItems, kRankBallot, 3>(
+            "sort", CsrPassArgs{kin, vin, ko, vo, m, p, U(L.dstart),
+                                reinterpret_cast<uint64_t *>(b + L.status), U(L.counters),
+                                dev->status, nullptr, 0, nullptr, nullptr, nullptr, d, base},
+            stream);
         kin = ko;
         vin = vo;
     }
@@ -786,25 +856,18 @@ extern "C" boba_status_t boba_coo_to_csr(const int32_t *src, const int32_t *dst,
         float *val_p = fuse ? val_out : nullptr;
         const uint32_t *od_in = fuse ? outdeg : nullptr;
         const int tv = tuned_variant(kTuneCsr, m);
-        // 0 (default): ballot ranking with registers capped for three resident
-        // blocks per SM; 1: ballot ranking, two blocks; 2: match ranking
-        if (tv == 1)
-            BOBA_TIMED("csr.pass", stream,
-                       k_csr_pass<kPassBlock, kPassItems, true><<<(unsigned)L.tiles, kPassBlock, 0,
-                                                                 stream>>>(
-                           kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status, p, 0, od, nn,
-                           od_in, val_p, ends_p));
-        else if (tv == 2)
-            BOBA_TIMED("csr.pass", stream,
-                       k_csr_pass<kPassBlock, kPassItems><<<(unsigned)L.tiles, kPassBlock, 0, stream>>>(
-                           kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status, p, 0, od, nn,
-                           od_in, val_p, ends_p));
-        else
-            BOBA_TIMED("csr.pass", stream,
-                       k_csr_pass<kPassBlock, kPassItems, true, 3><<<(unsigned)L.tiles, kPassBlock,
-                                                                    0, stream>>>(
-                           kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status, p, 0, od, nn,
-                           od_in, val_p, ends_p));
+        const CsrPassArgs pa{kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status, od, nn,
+                             od_in, val_p, ends_p, p, 0};
+        switch (tv) {
+        case 1: csr_pass_launch<512, 8, kRankBallot, 2>("csr.pass", pa, stream); break;
+        case 2: csr_pass_launch<512, 8, kRankMatch, 2>("csr.pass", pa, stream); break;
+        case 3: csr_pass_launch<512, 8, kRankOr, 3>("csr.pass", pa, stream); break;
+        case 4: csr_pass_launch<256, 16, kRankBallot, 3>("csr.pass", pa, stream); break;
+        case 5: csr_pass_launch<256, 16, kRankOr, 3>("csr.pass", pa, stream); break;
+        case 6: csr_pass_launch<384, 16, kRankBallot, 2>("csr.pass", pa, stream); break;
+        case 7: csr_pass_launch<512, 16, kRankBallot, 1>("csr.pass", pa, stream); break;
+        default: csr_pass_launch<512, 8, kRankBallot, 3>("csr.pass", pa, stream); break;
+        }
         kin = ko;
         vin = vo;
     }

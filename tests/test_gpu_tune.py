@@ -87,17 +87,29 @@ def test_tune_batched_and_spmv(boba):
     boba.tune_reset()
 
 
+CSR_RANKINGS = tuple(range(8))        # ranking x tile shape
+
+
 def test_csr_ranking_variants_bit_identical(boba):
     I, J = synth.rmat(17, 800_001, seed=35)
     n = 1 << 17
-    orp, ocol, oval = oracle.coo_to_csr(I, J, n)
-    for v in (0, 1, 2):
-        boba.load().boba_tune_set(boba.TUNE_CSR, len(I), v)
-        rp, col, val = boba.coo_to_csr(torch.from_numpy(I).cuda(), torch.from_numpy(J).cuda(), n)
-        boba.stream_status()
-        np.testing.assert_array_equal(rp.cpu().numpy(), orp)
-        np.testing.assert_array_equal(col.cpu().numpy(), ocol)
-        np.testing.assert_array_equal(val.cpu().numpy(), oval)
+    # a second graph whose digits are mostly equal: one hub row takes half the
+    # edges, so whole warps share a digit in every pass
+    rng = np.random.default_rng(36)
+    m2 = 300_017
+    I2 = rng.integers(0, n, m2, dtype=np.int32)
+    J2 = np.where(rng.random(m2) < 0.5, 70_000, rng.integers(0, n, m2)).astype(np.int32)
+    for I_, J_ in ((I, J), (I2, J2)):
+        orp, ocol, oval = oracle.coo_to_csr(I_, J_, n)
+        for v in CSR_RANKINGS:
+            boba.load().boba_tune_set(boba.TUNE_CSR, len(I_), v)
+            rp, col, val = boba.coo_to_csr(torch.from_numpy(I_).cuda(), torch.from_numpy(J_).cuda(),
+                                           n)
+            boba.stream_status()
+            np.testing.assert_array_equal(rp.cpu().numpy(), orp, err_msg=f"variant {v}")
+            np.testing.assert_array_equal(col.cpu().numpy(), ocol, err_msg=f"variant {v}")
+            np.testing.assert_array_equal(val.cpu().numpy(), oval, err_msg=f"variant {v}")
+        boba.load().boba_tune_set(boba.TUNE_CSR, len(I_), -1)
     ch = boba.tune_csr(torch.from_numpy(I).cuda(), torch.from_numpy(J).cuda(), n, reps=2)
-    assert ch["csr"] in (0, 1, 2)
+    assert ch["csr"] in CSR_RANKINGS
     boba.tune_reset()

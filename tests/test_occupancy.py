@@ -44,14 +44,26 @@ def pick(rep, *frags):
 
 
 def test_radix_pass_register_budgets():
+    """Every radix pass shape fits the resident blocks its launch bounds ask
+    for; the 512 x 8 shapes (the default, the dst sort and the NBR sorts) keep
+    the budgets their measured occupancy relies on."""
     rep = ptxas_report("csr.cu")
     passes = pick(rep, "k_csr_pass")
     assert passes, "no radix pass kernels found"
+    shapes = set()
     for name, (regs, spill) in passes.items():
-        three = "Li3E" in name                      # capped for three blocks of 512 per SM
-        assert regs <= (40 if three else 64), (name, regs)
-        if not three:
-            assert spill <= 8, (name, spill)
+        m = re.search(r"k_csr_passILi(\d+)ELi(\d+)ELi(\d+)ELi(\d+)E", name)
+        assert m, name
+        block, items, rank, minb = map(int, m.groups())
+        shapes.add((block, items, rank, minb))
+        assert regs * block * minb <= 65536, (name, regs)
+        if (block, items) == (512, 8):
+            assert regs <= (40 if minb == 3 else 64), (name, regs)
+            if minb == 2:
+                assert spill <= 8, (name, spill)
+        else:
+            assert spill <= 32, (name, spill)
+    assert (512, 8, 1, 3) in shapes                   # the default: ballots, three blocks
 
 
 def test_spmv_and_reorder_register_budgets():
