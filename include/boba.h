@@ -527,8 +527,10 @@ boba_status_t boba_tune_spmv(const int64_t *row_ptr, const int32_t *col, const f
  * bit-ballots, registers capped for three blocks per SM; 1: the same with two
  * blocks; 2: one warp match instruction; 3: per-warp shared-memory OR masks of
  * the lanes holding each digit; 4 and 5: ballots and OR masks in 256 x 16
- * tiles; 6: ballots in 384 x 16 tiles; 7: ballots in 512 x 16 tiles), keyed
- * by m; every variant's CSR must equal the default's bit for bit.
+ * tiles; 6: ballots in 384 x 16 tiles; 7: ballots in 512 x 16 tiles; 8 and
+ * 9: variants 0 and 5 with the tiles' digit offsets taken from a count pass
+ * and a scan of the counts instead of the look-back), keyed by m; every
+ * variant's CSR must equal the default's bit for bit.
  */
 boba_status_t boba_tune_csr(const int32_t *src, const int32_t *dst, int64_t m, int64_t n,
                             int64_t *row_ptr, int32_t *col_out, float *val_out, void *ws,

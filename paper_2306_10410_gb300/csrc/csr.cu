@@ -9,12 +9,15 @@
 //                   warp match, or per-warp shared-memory OR masks of the
 //                   lanes holding each digit, + per-warp digit counters,
 //                   items striped so processing order is input order),
-//                   per-digit decoupled
-//                   look-back across tiles, and a scatter staged through
-//                   shared memory so that runs of equal
-//                   digits are written contiguously (Adinets and Merrill,
-//                   "Onesweep", 2022, for the single-pass scheme); the first
-//                   pass also counts outdeg(u) over the sources it carries
+//                   per-digit decoupled look-back across tiles, and a
+//                   scatter staged through shared memory so that runs of
+//                   equal digits are written contiguously (Adinets and
+//                   Merrill, "Onesweep", 2022, for the single-pass scheme);
+//                   the first pass also counts outdeg(u) over the sources it
+//                   carries
+//   k_tile_counts,  the reduce-then-scan alternative to the look-back (tuner
+//   k_tile_chunk_sums, variants): per-tile digit counts, then a column scan
+//   k_tile_apply    of them that gives each tile its digit runs' starts
 //   k_csr_ends      ends[k] = one past the last sorted entry of row k, and
 //                   val = fp32(1 / outdeg(col)); with two or more passes the
 //                   last pass does this itself as it writes its output
@@ -129,14 +132,16 @@ __global__ void __launch_bounds__(256) k_csr_digits(const uint32_t *__restrict__
 
 // One stable LSD pass over digit p (bits 8p .. 8p+7).  BLOCK threads hold
 // ITEMS items each; the first 256 threads also own one digit each for the
-// cross-tile look-back.
-template <int BLOCK, int ITEMS, int RANK = kRankMatch, int MINB = 2>
+// cross-tile look-back.  With PRESCAN the global start of each of the tile's
+// digit runs is read from tile_base[tile][d] (k_tile_counts, k_tile_chunk_sums
+// and k_tile_apply computed it before the pass) instead of the look-back.
+template <int BLOCK, int ITEMS, int RANK = kRankMatch, int MINB = 2, bool PRESCAN = false>
 __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
     const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint32_t *__restrict__ kout,
     uint32_t *__restrict__ vout, int64_t m, int p, const uint32_t *__restrict__ dstart,
     uint64_t *status_lb, uint32_t *counters, uint32_t *status, int digit, int base_shift,
     uint32_t *outdeg = nullptr, uint32_t n = 0, const uint32_t *outdeg_in = nullptr,
-    float *val_out = nullptr, uint32_t *ends = nullptr)
+    float *val_out = nullptr, uint32_t *ends = nullptr, const uint32_t *tile_base = nullptr)
 {
     constexpr int TILE = BLOCK * ITEMS;
     constexpr int WARPS = BLOCK / 32;
@@ -155,12 +160,13 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
     __shared__ uint32_t s_tile;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_tile = atomicAdd(&counters[p], 1u);
+    if constexpr (!PRESCAN)
+        if (threadIdx.x == 0) s_tile = atomicAdd(&counters[p], 1u);
     for (int i = threadIdx.x; i < WARPS * 256; i += BLOCK) (&s_wcnt[0][0])[i] = 0;
     if constexpr (RANK == kRankOr)
         for (int i = threadIdx.x; i < WARPS * NBIN; i += BLOCK) (&s_bins[0][0])[i] = 0;
     __syncthreads();
-    const int64_t tile = s_tile;
+    const int64_t tile = PRESCAN ? (int64_t)blockIdx.x : (int64_t)s_tile;
     const int64_t t0 = tile * TILE;
     const int shift = base_shift + 8 * digit;
     // items of this tile; tile-local indices and global positions fit 32 bits
@@ -246,7 +252,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
     }
     uint32_t tot;
     const uint32_t tpre = BlockScan<BLOCK>::exclusive(cnt, &tot, sm);
-    if (d < 256) {
+    if (d < 256 && PRESCAN) {
+        s_tpre[d] = tpre;
+        s_base[d] = tile_base[tile * 256 + d];
+    } else if (d < 256) {
         s_tpre[d] = tpre;
         // per-digit look-back across tiles, reading 8 predecessors per round trip
         uint64_t *st = status_lb + tile * 256 + d;
@@ -341,6 +350,76 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
     }
 }
 
+// Reduce-then-scan alternative to the look-back (the PRESCAN passes):
+// counts[t][d] = items of tile t (the pass's tiles) whose digit is d.
+template <int BLOCK, int ITEMS>
+__global__ void __launch_bounds__(BLOCK) k_tile_counts(const uint32_t *__restrict__ kin, int64_t m,
+                                                       int shift, uint32_t *__restrict__ counts)
+{
+    constexpr int TILE = BLOCK * ITEMS;
+    constexpr int WARPS = BLOCK / 32;
+    __shared__ uint32_t s_h[WARPS][256];          // one histogram per warp
+    for (int i = threadIdx.x; i < WARPS * 256; i += BLOCK) (&s_h[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t t0 = (int64_t)blockIdx.x * TILE;
+    const int valid_n = (m - t0) < TILE ? (int)(m - t0) : TILE;
+    const uint32_t *kin_t = kin + t0;
+    const int warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+        const int j = k * BLOCK + threadIdx.x;
+        if (j < valid_n) atomicAdd(&s_h[warp][(kin_t[j] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += BLOCK) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) c += s_h[w][d];
+        counts[(int64_t)blockIdx.x * 256 + d] = c;
+    }
+}
+
+constexpr int kChunkTiles = 256;                 // tiles per block of the count scan
+
+// csum[c][d] = sum of counts[t][d] over the kChunkTiles tiles of chunk c.
+__global__ void __launch_bounds__(256) k_tile_chunk_sums(const uint32_t *__restrict__ counts,
+                                                         int64_t tiles, uint32_t *__restrict__ csum)
+{
+    const int d = threadIdx.x;
+    const int64_t c = blockIdx.x;
+    const int64_t t1 = (c + 1) * kChunkTiles < tiles ? (c + 1) * kChunkTiles : tiles;
+    uint32_t s = 0;
+#pragma unroll 16
+    for (int64_t t = c * kChunkTiles; t < t1; ++t) s += counts[t * 256 + d];
+    csum[c * 256 + d] = s;
+}
+
+// counts[t][d] <- dstart[d] + the sum of counts[t'][d] over t' < t: the
+// global position where tile t's run of digit d starts.
+__global__ void __launch_bounds__(256) k_tile_apply(uint32_t *counts, int64_t tiles,
+                                                    const uint32_t *__restrict__ csum,
+                                                    const uint32_t *__restrict__ dstart_p)
+{
+    const int d = threadIdx.x;
+    const int64_t c = blockIdx.x;
+    uint32_t base = dstart_p[d];
+#pragma unroll 8
+    for (int64_t q = 0; q < c; ++q) base += csum[q * 256 + d];
+    const int64_t t_begin = c * kChunkTiles;
+    const int64_t t1 = t_begin + kChunkTiles < tiles ? t_begin + kChunkTiles : tiles;
+    constexpr int G = 16;                         // rows loaded before they are rewritten
+    for (int64_t t = t_begin; t < t1; t += G) {
+        uint32_t v[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) v[g] = t + g < t1 ? counts[(t + g) * 256 + d] : 0u;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            if (t + g < t1) counts[(t + g) * 256 + d] = base;
+            base += v[g];
+        }
+    }
+}
+
 // One radix pass of the CSR build in a given shape (the tuner's variants).
 // Every shape's tile holds at least kPassTile items, so the look-back status
 // array sized for kPassTile tiles serves all of them.
@@ -359,7 +438,7 @@ struct CsrPassArgs {
     int digit = 0, base_shift = 0;   // key bits base_shift + 8 digit .. + 7; 0, 0: digit p
 };
 
-template <int BLOCK, int ITEMS, int RANK, int MINB>
+template <int BLOCK, int ITEMS, int RANK, int MINB, bool PRESCAN = false>
 void csr_pass_launch(const char *name, const CsrPassArgs &a, cudaStream_t stream)
 {
     constexpr int TILE = BLOCK * ITEMS;
@@ -373,15 +452,32 @@ void csr_pass_launch(const char *name, const CsrPassArgs &a, cudaStream_t stream
     cudaGetDevice(&dev);
     const uint64_t bit = 1ull << (dev & 63);
     if ((done.load() & bit) == 0) {
-        cudaFuncSetAttribute((const void *)k_csr_pass<BLOCK, ITEMS, RANK, MINB>,
+        cudaFuncSetAttribute((const void *)k_csr_pass<BLOCK, ITEMS, RANK, MINB, PRESCAN>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         done.fetch_or(bit);
     }
     const unsigned tiles = (unsigned)cdiv(a.m > 0 ? a.m : 1, TILE);
+    uint32_t *tile_base = nullptr;
+    if constexpr (PRESCAN) {
+        // the look-back status array (8 bytes per tile and digit of kPassTile
+        // tiles) holds the counts (4 bytes per tile and digit) and the chunk sums
+        tile_base = reinterpret_cast<uint32_t *>(a.lb);
+        uint32_t *csum = tile_base + (size_t)tiles * 256;
+        const unsigned chunks = (unsigned)cdiv(tiles, kChunkTiles);
+        BOBA_TIMED("csr.prescan", stream,
+                   k_tile_counts<BLOCK, ITEMS><<<tiles, BLOCK, 0, stream>>>(
+                       a.kin, a.m, a.base_shift + 8 * a.digit, tile_base));
+        BOBA_TIMED("csr.prescan", stream,
+                   k_tile_chunk_sums<<<chunks, 256, 0, stream>>>(tile_base, tiles, csum));
+        BOBA_TIMED("csr.prescan", stream,
+                   k_tile_apply<<<chunks, 256, 0, stream>>>(tile_base, tiles, csum,
+                                                            a.dstart + a.digit * 256));
+    }
     BOBA_TIMED(name, stream,
-               k_csr_pass<BLOCK, ITEMS, RANK, MINB><<<tiles, BLOCK, smem, stream>>>(
+               k_csr_pass<BLOCK, ITEMS, RANK, MINB, PRESCAN><<<tiles, BLOCK, smem, stream>>>(
                    a.kin, a.vin, a.kout, a.vout, a.m, a.p, a.dstart, a.lb, a.ctr, a.status,
-                   a.digit, a.base_shift, a.outdeg, a.n, a.outdeg_in, a.val_out, a.ends));
+                   a.digit, a.base_shift, a.outdeg, a.n, a.outdeg_in, a.val_out, a.ends,
+                   tile_base));
 }
 
 // ends[k] = 1 + index of the last sorted entry with key k (0 if none);
@@ -866,6 +962,8 @@ extern "C" boba_status_t boba_coo_to_csr(const int32_t *src, const int32_t *dst,
         case 5: csr_pass_launch<256, 16, kRankOr, 3>("csr.pass", pa, stream); break;
         case 6: csr_pass_launch<384, 16, kRankBallot, 2>("csr.pass", pa, stream); break;
         case 7: csr_pass_launch<512, 16, kRankBallot, 1>("csr.pass", pa, stream); break;
+        case 8: csr_pass_launch<512, 8, kRankBallot, 3, true>("csr.pass", pa, stream); break;
+        case 9: csr_pass_launch<256, 16, kRankOr, 3, true>("csr.pass", pa, stream); break;
         default: csr_pass_launch<512, 8, kRankBallot, 3>("csr.pass", pa, stream); break;
         }
         kin = ko;

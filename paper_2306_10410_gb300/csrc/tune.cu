@@ -25,7 +25,7 @@ namespace {
 
 constexpr int kClasses = 64;
 constexpr int kMaxDev = 64;
-constexpr int kVariants[kTuneKernels] = {6, 6, 6, 14, 8};   // first, relabel, batched, spmv, csr
+constexpr int kVariants[kTuneKernels] = {6, 6, 6, 14, 10};   // first, relabel, batched, spmv, csr
 const char *kNames[kTuneKernels] = {"first", "relabel", "batched", "spmv", "csr"};
 
 std::mutex g_tmu;

@@ -87,7 +87,7 @@ def test_tune_batched_and_spmv(boba):
     boba.tune_reset()
 
 
-CSR_RANKINGS = tuple(range(8))        # ranking x tile shape
+CSR_RANKINGS = tuple(range(10))       # ranking x tile shape x look-back or prescan
 
 
 def test_csr_ranking_variants_bit_identical(boba):
