@@ -42,6 +42,7 @@ constexpr int kMaxPasses = 4;                        // 32-bit keys
 // shared-memory mask of its digit and reads the mask back.
 constexpr int kRankMatch = 0, kRankBallot = 1, kRankOr = 2;
 constexpr int kNumCtr = 16;
+constexpr int kCountWarps = 8;                   // histogram kernels: 256 threads, a tile per warp
 
 // Look-back status of (tile, digit) for pass p, one u64: the top 4 bits hold
 // 2p+1 (aggregate) or 2p+2 (inclusive prefix); anything else (0, or an earlier
@@ -98,23 +99,85 @@ __global__ void __launch_bounds__(256) k_zero(uint4 *p, int64_t n16)
         p[i] = z;
 }
 
-// Digit histograms of every pass over dst.
-__global__ void __launch_bounds__(256) k_csr_hist(const int32_t *__restrict__ dst, int64_t m,
-                                                  uint32_t n, int passes, uint32_t *hist,
-                                                  uint32_t *status)
+// Digit histograms of every pass (8-bit digits from bit base_shift on) over
+// a key array, one warp per tile of TILE keys with warp-private shared
+// histograms, so warps never contend.  With tile_counts it also writes each
+// tile's counts of the first digit, which the reduce-then-scan first pass then
+// takes instead of its own count kernel.  Keys >= n (n > 0) are reported.
+template <int TILE>
+__global__ void __launch_bounds__(kCountWarps * 32) k_hist_tiles(
+    const uint32_t *__restrict__ keys, int64_t m, int digits, int base_shift, uint32_t n,
+    uint32_t *hist, uint32_t *__restrict__ tile_counts, uint32_t *status)
 {
-    __shared__ uint32_t sh[kMaxPasses * 256];
-    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x) sh[i] = 0;
+    __shared__ uint32_t s_run[kCountWarps][kMaxPasses * 256];   // per warp, all digits
+    __shared__ uint32_t s_tile[kCountWarps][256];               // per warp, one tile's first digit
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kCountWarps * kMaxPasses * 256; i += blockDim.x)
+        (&s_run[0][0])[i] = 0;
     __syncthreads();
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-        const uint32_t k = (uint32_t)ld_stream(dst + e);
-        for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * 256 + ((k >> (8 * p)) & 255u)], 1u);
-        if (k >= n) raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE);
+    uint32_t *run = s_run[warp], *th = s_tile[warp];
+    uint32_t *first = tile_counts != nullptr ? th : run;
+    const int64_t tiles = (m + TILE - 1) / TILE;
+    bool bad = false;
+    for (int64_t t = (int64_t)blockIdx.x * kCountWarps + warp; t < tiles;
+         t += (int64_t)gridDim.x * kCountWarps) {
+        if (tile_counts != nullptr) {
+#pragma unroll
+            for (int i = lane; i < 256; i += 32) th[i] = 0;
+            __syncwarp();
+        }
+        const int64_t t0 = t * TILE;
+        const int valid_n = (m - t0) < TILE ? (int)(m - t0) : TILE;
+        const uint32_t *k = keys + t0;
+        for (int base = 0; base < valid_n; base += 32 * 8) {
+            uint32_t v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = base + u * 32 + lane;
+                v[u] = j < valid_n ? k[j] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (base + u * 32 + lane < valid_n) {
+                    const uint32_t key = v[u];
+                    atomicAdd(&first[(key >> base_shift) & 255u], 1u);
+                    for (int d = 1; d < digits; ++d)
+                        atomicAdd(&run[d * 256 + ((key >> (base_shift + 8 * d)) & 255u)], 1u);
+                    bad |= n != 0 && key >= n;
+                }
+            }
+        }
+        __syncwarp();
+        if (tile_counts != nullptr) {
+#pragma unroll
+            for (int i = lane; i < 256; i += 32) {
+                const uint32_t c = th[i];
+                tile_counts[t * 256 + i] = c;
+                run[i] += c;
+            }
+            __syncwarp();
+        }
     }
+    if (bad) raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE);
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * 256; i += blockDim.x)
-        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+    for (int i = threadIdx.x; i < digits * 256; i += blockDim.x) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < kCountWarps; ++w) c += s_run[w][i];
+        if (c) atomicAdd(&hist[i], c);
+    }
+}
+
+// Launch of k_hist_tiles over the whole key array.
+void launch_hist(const char *name, const uint32_t *keys, int64_t m, int digits, int base_shift,
+                 uint32_t n, uint32_t *hist, uint32_t *tile_counts, uint32_t *status,
+                 cudaStream_t stream)
+{
+    const int g = persistent_grid((const void *)k_hist_tiles<kPassTile>, kCountWarps * 32,
+                                  cdiv(cdiv(m > 0 ? m : 1, kPassTile), kCountWarps));
+    BOBA_TIMED(name, stream,
+               k_hist_tiles<kPassTile><<<g, kCountWarps * 32, 0, stream>>>(
+                   keys, m, digits, base_shift, n, hist, tile_counts, status));
 }
 
 // dstart[p][d] = exclusive prefix of hist[p][.] (one block of 256 threads).
@@ -350,41 +413,59 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
     }
 }
 
-// Reduce-then-scan alternative to the look-back (the PRESCAN passes):
-// counts[t][d] = items of tile t (the pass's tiles) whose digit is d.
-template <int BLOCK, int ITEMS>
-__global__ void __launch_bounds__(BLOCK) k_tile_counts(const uint32_t *__restrict__ kin, int64_t m,
-                                                       int shift, uint32_t *__restrict__ counts)
+// Reduce-then-scan alternative to the look-back (the PRESCAN passes).
+constexpr int kChunkTiles = 256;                 // tiles per block of the count scan
+constexpr int kCtrPrescan = 12;                  // counters slot: ticket of the chunk-sum blocks
+
+// counts[t][d] = items of tile t (TILE items, the pass's tiles) whose digit is
+// d.  One warp counts a whole tile into a warp-private shared histogram, so
+// nothing but __syncwarp orders it; the grid strides over the tiles.
+template <int TILE>
+__global__ void __launch_bounds__(kCountWarps * 32) k_tile_counts(
+    const uint32_t *__restrict__ kin, int64_t m, int shift, int64_t tiles,
+    uint32_t *__restrict__ counts)
 {
-    constexpr int TILE = BLOCK * ITEMS;
-    constexpr int WARPS = BLOCK / 32;
-    __shared__ uint32_t s_h[WARPS][256];          // one histogram per warp
-    for (int i = threadIdx.x; i < WARPS * 256; i += BLOCK) (&s_h[0][0])[i] = 0;
-    __syncthreads();
-    const int64_t t0 = (int64_t)blockIdx.x * TILE;
-    const int valid_n = (m - t0) < TILE ? (int)(m - t0) : TILE;
-    const uint32_t *kin_t = kin + t0;
-    const int warp = threadIdx.x >> 5;
+    __shared__ uint32_t s_h[kCountWarps][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *h = s_h[warp];
+    for (int64_t t = (int64_t)blockIdx.x * kCountWarps + warp; t < tiles;
+         t += (int64_t)gridDim.x * kCountWarps) {
 #pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-        const int j = k * BLOCK + threadIdx.x;
-        if (j < valid_n) atomicAdd(&s_h[warp][(kin_t[j] >> shift) & 255u], 1u);
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < 256; d += BLOCK) {
-        uint32_t c = 0;
+        for (int i = lane; i < 256; i += 32) h[i] = 0;
+        __syncwarp();
+        const int64_t t0 = t * TILE;
+        const int valid_n = (m - t0) < TILE ? (int)(m - t0) : TILE;
+        const uint32_t *k = kin + t0;
+        for (int base = 0; base < valid_n; base += 32 * 8) {
+            uint32_t v[8];
 #pragma unroll
-        for (int w = 0; w < WARPS; ++w) c += s_h[w][d];
-        counts[(int64_t)blockIdx.x * 256 + d] = c;
+            for (int u = 0; u < 8; ++u) {
+                const int j = base + u * 32 + lane;
+                v[u] = j < valid_n ? k[j] : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (base + u * 32 + lane < valid_n) atomicAdd(&h[(v[u] >> shift) & 255u], 1u);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int i = lane; i < 256; i += 32) counts[t * 256 + i] = h[i];
+        __syncwarp();
     }
 }
 
-constexpr int kChunkTiles = 256;                 // tiles per block of the count scan
-
-// csum[c][d] = sum of counts[t][d] over the kChunkTiles tiles of chunk c.
+// csum[c][d] = sum of counts[t][d] over the kChunkTiles tiles of chunk c; the
+// last block to finish (by ticket) then rewrites csum[c][d] as dstart[d] plus
+// the sum over the chunks before c: where chunk c's run of digit d starts.
+// The ticket starts at 0 (the workspace is cleared) and the last block puts it
+// back to 0 for the next pass.
 __global__ void __launch_bounds__(256) k_tile_chunk_sums(const uint32_t *__restrict__ counts,
-                                                         int64_t tiles, uint32_t *__restrict__ csum)
+                                                         int64_t tiles, int64_t chunks,
+                                                         uint32_t *csum,
+                                                         const uint32_t *__restrict__ dstart_p,
+                                                         uint32_t *ticket)
 {
+    __shared__ bool s_last;
     const int d = threadIdx.x;
     const int64_t c = blockIdx.x;
     const int64_t t1 = (c + 1) * kChunkTiles < tiles ? (c + 1) * kChunkTiles : tiles;
@@ -392,19 +473,34 @@ __global__ void __launch_bounds__(256) k_tile_chunk_sums(const uint32_t *__restr
 #pragma unroll 16
     for (int64_t t = c * kChunkTiles; t < t1; ++t) s += counts[t * 256 + d];
     csum[c * 256 + d] = s;
+    __threadfence();
+    __syncthreads();
+    if (d == 0) s_last = atomicAdd(ticket, 1u) == (uint32_t)chunks - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (d == 0) *ticket = 0;
+    uint32_t base = dstart_p[d];
+    for (int64_t q = 0; q < chunks; q += 16) {
+        uint32_t v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) v[u] = q + u < chunks ? __ldcg(&csum[(q + u) * 256 + d]) : 0u;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            if (q + u < chunks) csum[(q + u) * 256 + d] = base;
+            base += v[u];
+        }
+    }
 }
 
-// counts[t][d] <- dstart[d] + the sum of counts[t'][d] over t' < t: the
-// global position where tile t's run of digit d starts.
+// counts[t][d] <- where tile t's run of digit d starts: its chunk's start plus
+// the counts of the chunk's earlier tiles.
 __global__ void __launch_bounds__(256) k_tile_apply(uint32_t *counts, int64_t tiles,
-                                                    const uint32_t *__restrict__ csum,
-                                                    const uint32_t *__restrict__ dstart_p)
+                                                    const uint32_t *__restrict__ cbase)
 {
     const int d = threadIdx.x;
     const int64_t c = blockIdx.x;
-    uint32_t base = dstart_p[d];
-#pragma unroll 8
-    for (int64_t q = 0; q < c; ++q) base += csum[q * 256 + d];
+    uint32_t base = cbase[c * 256 + d];
     const int64_t t_begin = c * kChunkTiles;
     const int64_t t1 = t_begin + kChunkTiles < tiles ? t_begin + kChunkTiles : tiles;
     constexpr int G = 16;                         // rows loaded before they are rewritten
@@ -436,6 +532,7 @@ struct CsrPassArgs {
     float *val_out;
     uint32_t *ends;
     int digit = 0, base_shift = 0;   // key bits base_shift + 8 digit .. + 7; 0, 0: digit p
+    bool counts_ready = false;       // the tile counts are in place (k_hist_tiles wrote them)
 };
 
 template <int BLOCK, int ITEMS, int RANK, int MINB, bool PRESCAN = false>
@@ -464,20 +561,38 @@ void csr_pass_launch(const char *name, const CsrPassArgs &a, cudaStream_t stream
         tile_base = reinterpret_cast<uint32_t *>(a.lb);
         uint32_t *csum = tile_base + (size_t)tiles * 256;
         const unsigned chunks = (unsigned)cdiv(tiles, kChunkTiles);
+        uint32_t *ticket = a.ctr + kCtrPrescan;
+        const int gc = persistent_grid((const void *)k_tile_counts<TILE>, kCountWarps * 32,
+                                       cdiv(tiles, kCountWarps));
+        static_assert(TILE == kPassTile, "k_hist_tiles writes the first pass's counts per kPassTile");
+        if (!a.counts_ready)
+            BOBA_TIMED("csr.prescan", stream,
+                       k_tile_counts<TILE><<<gc, kCountWarps * 32, 0, stream>>>(
+                           a.kin, a.m, a.base_shift + 8 * a.digit, tiles, tile_base));
         BOBA_TIMED("csr.prescan", stream,
-                   k_tile_counts<BLOCK, ITEMS><<<tiles, BLOCK, 0, stream>>>(
-                       a.kin, a.m, a.base_shift + 8 * a.digit, tile_base));
+                   k_tile_chunk_sums<<<chunks, 256, 0, stream>>>(
+                       tile_base, tiles, chunks, csum, a.dstart + a.digit * 256, ticket));
         BOBA_TIMED("csr.prescan", stream,
-                   k_tile_chunk_sums<<<chunks, 256, 0, stream>>>(tile_base, tiles, csum));
-        BOBA_TIMED("csr.prescan", stream,
-                   k_tile_apply<<<chunks, 256, 0, stream>>>(tile_base, tiles, csum,
-                                                            a.dstart + a.digit * 256));
+                   k_tile_apply<<<chunks, 256, 0, stream>>>(tile_base, tiles, csum));
     }
     BOBA_TIMED(name, stream,
                k_csr_pass<BLOCK, ITEMS, RANK, MINB, PRESCAN><<<tiles, BLOCK, smem, stream>>>(
                    a.kin, a.vin, a.kout, a.vout, a.m, a.p, a.dstart, a.lb, a.ctr, a.status,
                    a.digit, a.base_shift, a.outdeg, a.n, a.outdeg_in, a.val_out, a.ends,
                    tile_base));
+}
+
+// The pass the NBR sorts and boba_sort_by_dst use: the default shape, with
+// the reduce-then-scan offsets from 2^22 keys on (measured faster there; the
+// three extra launches per pass cost more than they save below).
+constexpr int64_t kPrescanMin = 1ll << 22;
+
+void sort_pass(const char *name, const CsrPassArgs &a, cudaStream_t stream)
+{
+    if (a.m >= kPrescanMin)
+        csr_pass_launch<kPassBlock, kPassItems, kRankBallot, 3, true>(name, a, stream);
+    else
+        csr_pass_launch<kPassBlock, kPassItems, kRankBallot, 3>(name, a, stream);
 }
 
 // ends[k] = 1 + index of the last sorted entry with key k (0 if none);
@@ -567,24 +682,6 @@ __global__ void k_rowptr_zero(int64_t *row_ptr, int64_t n)
 // stable radix sorts (by column, then by row), after which distinct values
 // and distinct lines are counted by comparing neighbours.
 // ---------------------------------------------------------------------------
-
-// Digit histograms (8-bit digits 0 .. digits-1) of a key array.
-__global__ void __launch_bounds__(256) k_digit_hist(const uint32_t *__restrict__ keys, int64_t m,
-                                                    int digits, uint32_t *hist, int base_shift)
-{
-    __shared__ uint32_t sh[kMaxPasses * 256];
-    for (int i = threadIdx.x; i < digits * 256; i += blockDim.x) sh[i] = 0;
-    __syncthreads();
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t k = __ldcs(keys + e);
-        for (int d = 0; d < digits; ++d)
-            atomicAdd(&sh[d * 256 + ((k >> (base_shift + 8 * d)) & 255u)], 1u);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < digits * 256; i += blockDim.x)
-        if (sh[i]) atomicAdd(&hist[i], sh[i]);
-}
 
 // rows[p] = r for every entry p of row r (a warp per row).
 __global__ void __launch_bounds__(256) k_expand_rows(const int64_t *__restrict__ row_ptr,
@@ -731,21 +828,21 @@ extern "C" boba_status_t boba_nbr(const int64_t *row_ptr, const int32_t *col, in
     BOBA_TIMED("nbr", stream, k_zero<<<gz, 256, 0, stream>>>(reinterpret_cast<uint4 *>(b + L.zero_begin), zero16));
     const int gr = persistent_grid((const void *)k_expand_rows, 256, cdiv(n_rows * 32, 256));
     BOBA_TIMED("nbr", stream, k_expand_rows<<<gr, 256, 0, stream>>>(row_ptr, n_rows, U(L.rows)));
-    const int gh = persistent_grid((const void *)k_digit_hist, 256, cdiv(nnz, 256));
-    BOBA_TIMED("nbr", stream,
-               k_digit_hist<<<gh, 256, 0, stream>>>(reinterpret_cast<const uint32_t *>(col), nnz,
-                                                    L.passes, U(L.hist1), 0));
-    BOBA_TIMED("nbr", stream,
-               k_digit_hist<<<gh, 256, 0, stream>>>(U(L.rows), nnz, L.passes, U(L.hist2), 0));
+    // the first sort's pass 0 reads col in this order, so its tile counts come
+    // with the histogram; the second sort's input order is the first's output
+    const bool pre = nnz >= kPrescanMin;
+    launch_hist("nbr", reinterpret_cast<const uint32_t *>(col), nnz, L.passes, 0, 0u, U(L.hist1),
+                pre ? reinterpret_cast<uint32_t *>(lb) : nullptr, dev->status, stream);
+    launch_hist("nbr", U(L.rows), nnz, L.passes, 0, 0u, U(L.hist2), nullptr, dev->status, stream);
     BOBA_TIMED("nbr", stream, k_csr_digits<<<1, 256, 0, stream>>>(U(L.hist1), U(L.dst1), L.passes));
     BOBA_TIMED("nbr", stream, k_csr_digits<<<1, 256, 0, stream>>>(U(L.hist2), U(L.dst2), L.passes));
     // sort 1: by column (values: rows)
     const uint32_t *kin = reinterpret_cast<const uint32_t *>(col), *vin = U(L.rows);
     for (int p = 0; p < L.passes; ++p) {
         uint32_t *ko = (p & 1) ? U(L.kB) : U(L.kA), *vo = (p & 1) ? U(L.vB) : U(L.vA);
-        csr_pass_launch<kPassBlock, kPassItems, kRankBallot, 3>(
+        sort_pass(
             "nbr", CsrPassArgs{kin, vin, ko, vo, nnz, p, U(L.dst1), lb, U(L.counters), dev->status,
-                               nullptr, 0, nullptr, nullptr, nullptr, p, 0},
+                               nullptr, 0, nullptr, nullptr, nullptr, p, 0, p == 0},
             stream);
         kin = ko;
         vin = vo;
@@ -764,7 +861,7 @@ extern "C" boba_status_t boba_nbr(const int64_t *row_ptr, const int32_t *col, in
     vin = cbuf;
     for (int p = 0; p < L.passes; ++p) {
         uint32_t *ko = (p & 1) ? rbuf : fb[0], *vo = (p & 1) ? cbuf : fb[1];
-        csr_pass_launch<kPassBlock, kPassItems, kRankBallot, 3>(
+        sort_pass(
             "nbr", CsrPassArgs{kin, vin, ko, vo, nnz, p, U(L.dst2), lb, U(L.counters), dev->status,
                                nullptr, 0, nullptr, nullptr, nullptr, p, 0},
             stream);
@@ -861,10 +958,8 @@ extern "C" boba_status_t boba_sort_by_dst(const int32_t *src, const int32_t *dst
     // significant bits of a ceil(log2 n)-bit ID
     const int digits = top_digit_only ? 1 : L.passes;
     const int base = top_digit_only ? (L.bits > 8 ? L.bits - 8 : 0) : 0;
-    const int gh = persistent_grid((const void *)k_digit_hist, 256, cdiv(m, 256));
-    BOBA_TIMED("sort", stream,
-               k_digit_hist<<<gh, 256, 0, stream>>>(reinterpret_cast<const uint32_t *>(dst), m,
-                                                    digits, U(L.hist), base));
+    launch_hist("sort", reinterpret_cast<const uint32_t *>(dst), m, digits, base, 0u, U(L.hist),
+                m >= kPrescanMin ? U(L.status) : nullptr, dev->status, stream);
     BOBA_TIMED("sort", stream, k_csr_digits<<<1, 256, 0, stream>>>(U(L.hist), U(L.dstart), digits));
     const uint32_t *kin = reinterpret_cast<const uint32_t *>(dst);
     const uint32_t *vin = reinterpret_cast<const uint32_t *>(src);
@@ -872,10 +967,11 @@ extern "C" boba_status_t boba_sort_by_dst(const int32_t *src, const int32_t *dst
         const bool last = d == digits - 1;
         uint32_t *ko = last ? reinterpret_cast<uint32_t *>(dst_out) : ((p & 1) ? U(L.kB) : U(L.kA));
         uint32_t *vo = last ? reinterpret_cast<uint32_t *>(src_out) : ((p & 1) ? U(L.vB) : U(L.vA));
-        csr_pass_launch<kPassBlock, kPassItems, kRankBallot, 3>(
+        sort_pass(
             "sort", CsrPassArgs{kin, vin, ko, vo, m, p, U(L.dstart),
                                 reinterpret_cast<uint64_t *>(b + L.status), U(L.counters),
-                                dev->status, nullptr, 0, nullptr, nullptr, nullptr, d, base},
+                                dev->status, nullptr, 0, nullptr, nullptr, nullptr, d, base,
+                                d == 0},
             stream);
         kin = ko;
         vin = vo;
@@ -931,11 +1027,10 @@ extern "C" boba_status_t boba_coo_to_csr(const int32_t *src, const int32_t *dst,
         BOBA_TIMED("csr.zero", stream,
                    k_zero<<<g, 256, 0, stream>>>(reinterpret_cast<uint4 *>(b + L.zero_begin), n16));
     }
-    {
-        const int g = persistent_grid((const void *)k_csr_hist, 256, cdiv(m, 256));
-        BOBA_TIMED("csr.hist", stream,
-                   k_csr_hist<<<g, 256, 0, stream>>>(dst, m, nn, L.passes, hist, dev->status));
-    }
+    const int tv = tuned_variant(kTuneCsr, m);
+    const bool prescan = tv == 8 || tv == 9;        // the reduce-then-scan shapes (tiles of kPassTile)
+    launch_hist("csr.hist", reinterpret_cast<const uint32_t *>(dst), m, L.passes, 0, nn, hist,
+                prescan ? reinterpret_cast<uint32_t *>(lb) : nullptr, dev->status, stream);
     BOBA_TIMED("csr.digits", stream,
                k_csr_digits<<<1, 256, 0, stream>>>(hist, dstart, L.passes));
     const uint32_t *kin = reinterpret_cast<const uint32_t *>(dst);
@@ -951,9 +1046,8 @@ extern "C" boba_status_t boba_coo_to_csr(const int32_t *src, const int32_t *dst,
         uint32_t *ends_p = fuse ? ends : nullptr;
         float *val_p = fuse ? val_out : nullptr;
         const uint32_t *od_in = fuse ? outdeg : nullptr;
-        const int tv = tuned_variant(kTuneCsr, m);
         const CsrPassArgs pa{kin, vin, ko, vo, m, p, dstart, lb, ctr, dev->status, od, nn,
-                             od_in, val_p, ends_p, p, 0};
+                             od_in, val_p, ends_p, p, 0, prescan && p == 0};
         switch (tv) {
         case 1: csr_pass_launch<512, 8, kRankBallot, 2>("csr.pass", pa, stream); break;
         case 2: csr_pass_launch<512, 8, kRankMatch, 2>("csr.pass", pa, stream); break;

@@ -147,6 +147,17 @@ def test_full_size_rmat24_csr_spmv(boba):
     np.testing.assert_array_equal(col.cpu().numpy(), ocol)
     np.testing.assert_array_equal(val.cpu().numpy().view(np.uint32), oval.view(np.uint32))
     check_spmv(boba, (rp, col, val), (orp, ocol, oval), synth.uniform_f32(w.n, seed=w.seed))
+    # the radix-pass variants the tuner picks at this size, in the benchmark's
+    # configuration (OR masks; reduce-then-scan with either ranking)
+    for v in (5, 8, 9):
+        boba.load().boba_tune_set(boba.TUNE_CSR, w.m, v)
+        rp, col, val = boba.coo_to_csr(so, do, w.n)
+        boba.stream_status()
+        np.testing.assert_array_equal(rp.cpu().numpy(), orp, err_msg=f"variant {v}")
+        np.testing.assert_array_equal(col.cpu().numpy(), ocol, err_msg=f"variant {v}")
+        np.testing.assert_array_equal(val.cpu().numpy().view(np.uint32), oval.view(np.uint32),
+                                      err_msg=f"variant {v}")
+    boba.load().boba_tune_set(boba.TUNE_CSR, w.m, -1)
 
 
 @pytest.mark.parametrize("variant", list(range(14)))

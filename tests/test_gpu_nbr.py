@@ -54,20 +54,29 @@ def test_long_rows_and_wide_ids(boba):
 
 
 def test_boba_improves_locality_on_rmat(boba):
-    I, J = synth.rmat(18, 1 << 22, seed=8)
+    """2^22 + a ragged tail of nonzeros: the NBR sorts take the reduce-then-scan
+    passes there; the values equal the oracle's."""
+    m = (1 << 22) + 12_347
+    I, J = synth.rmat(18, m, seed=8)
     n = 1 << 18
     _, Io, Jo = oracle.reorder(I, J, n)
-    vr, _ = boba.nbr(*[dev(a) for a in oracle.coo_to_csr(I, J, n)[:2]])
-    vb, _ = boba.nbr(*[dev(a) for a in oracle.coo_to_csr(Io, Jo, n)[:2]])
+    csr_r, csr_b = oracle.coo_to_csr(I, J, n), oracle.coo_to_csr(Io, Jo, n)
+    vr, cr = boba.nbr(*[dev(a) for a in csr_r[:2]])
+    vb, cb = boba.nbr(*[dev(a) for a in csr_b[:2]])
+    for (v, c), csr in (((vr, cr), csr_r), ((vb, cb), csr_b)):
+        ov, oc = oracle.nbr(csr[0], csr[1], 32)
+        assert c == oc and abs(v - ov) <= 1e-12 * max(1.0, ov)
     assert vb < vr
 
 
+@pytest.mark.parametrize("m", [(1 << 22) - 1, (1 << 22) + 4099])
 @pytest.mark.parametrize("bin_only", [False, True])
-def test_sort_by_dst_then_boba(boba, bin_only):
+def test_sort_by_dst_then_boba(boba, bin_only, m):
     """Sec. 5.6: sorting (or binning) a randomly ordered edge list by destination
-    before BOBA.  The sort is bit-exact; afterwards BOBA lowers NBR below both
-    the random order and BOBA on the random order."""
-    I, J = synth.rmat(18, 1 << 22, seed=9)
+    before BOBA.  The sort is bit-exact (on both sides of the size where its
+    passes switch from the look-back to reduce-then-scan); afterwards BOBA
+    lowers NBR below both the random order and BOBA on the random order."""
+    I, J = synth.rmat(18, m, seed=9)
     n = 1 << 18
     so, do = boba.sort_by_dst(dev(I), dev(J), n, bin_only=bin_only)
     boba.stream_status()
