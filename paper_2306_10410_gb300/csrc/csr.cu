@@ -3,7 +3,9 @@
 // edge order, and the entry of edge u -> v holds fp32(1 / outdeg(u)).
 //
 // A stable LSD radix sort of (key = dst, value = src) with 8-bit digits:
-//   k_csr_hist      per-digit histograms of all passes in one read of dst
+//   k_hist_tiles    per-digit histograms of all passes in one read of dst
+//                   (a tile per warp, warp-private shared histograms); for
+//                   the reduce-then-scan passes also pass 0's tile counts
 //   k_csr_digits    exclusive scan of each pass's 256 digit counts
 //   k_csr_pass      one pass: stable in-tile ranking (eight bit-ballots, one
 //                   warp match, or per-warp shared-memory OR masks of the
