@@ -524,7 +524,8 @@ boba_status_t boba_tune_spmv(const int64_t *row_ptr, const int32_t *col, const f
 /*
  * boba_tune_csr -- the same for the radix passes of boba_coo_to_csr: their
  * in-tile ranking and tile shape (variant 0: 512 threads x 8 keys, eight
- * bit-ballots, registers capped for three blocks per SM; 1: the same with two
+ * bit-ballots, registers capped for three blocks per SM, and from 2^22 keys on
+ * the reduce-then-scan form of it, variant 8; 1: the same with two
  * blocks; 2: one warp match instruction; 3: per-warp shared-memory OR masks of
  * the lanes holding each digit; 4 and 5: ballots and OR masks in 256 x 16
  * tiles; 6: ballots in 384 x 16 tiles; 7: ballots in 512 x 16 tiles; 8 and

@@ -1029,7 +1029,10 @@ extern "C" boba_status_t boba_coo_to_csr(const int32_t *src, const int32_t *dst,
         BOBA_TIMED("csr.zero", stream,
                    k_zero<<<g, 256, 0, stream>>>(reinterpret_cast<uint4 *>(b + L.zero_begin), n16));
     }
-    const int tv = tuned_variant(kTuneCsr, m);
+    // variant 0 (untuned): the look-back passes, or from kPrescanMin keys on
+    // their reduce-then-scan form (variant 8), measured faster there
+    int tv = tuned_variant(kTuneCsr, m);
+    if (tv == 0 && m >= kPrescanMin) tv = 8;
     const bool prescan = tv == 8 || tv == 9;        // the reduce-then-scan shapes (tiles of kPassTile)
     launch_hist("csr.hist", reinterpret_cast<const uint32_t *>(dst), m, L.passes, 0, nn, hist,
                 prescan ? reinterpret_cast<uint32_t *>(lb) : nullptr, dev->status, stream);
