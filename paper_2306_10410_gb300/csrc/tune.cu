@@ -2,7 +2,8 @@
 // (block size and loads in flight of the first-occurrence and relabel
 // streams, the schedule of the batched path, the SpMV kernel and shape --
 // lanes per row, or merge-path block, items and shared-memory carve-out --
-// and the ranking of the radix passes), time every variant on the caller's
+// and the ranking, tile shape and offset scheme (look-back or
+// reduce-then-scan) of the radix passes), time every variant on the caller's
 // data and keep the fastest for that size class (log2 of the size) on this
 // device.  Integer results must equal the default's bit for bit (a variant
 // that differs is skipped); the SpMV shapes differ only in the order of fp32
