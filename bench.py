@@ -91,7 +91,7 @@ def algorithmic_bytes(m: int, n: int, nnz: int):
         "reorder.scan": bitmap + bitmap // 8,      # read bitmap, write group prefix
         "reorder.emit": 4 * n + 4 * n + 4 * n,     # keys in, label + perm out
         "reorder.relabel": 16 * m + 4 * n,         # src,dst in; src_out,dst_out out; label
-        "csr.hist": 8 * m + 8 * n,
+        "csr.hist": 4 * m,                         # read dst (outdeg is counted in pass 0)
         "spmv": 8 * nnz + 16 * n,
     }
 
@@ -309,6 +309,18 @@ def run_ours(args):
     if have_csr:
         compare = compare_orders(args, boba, torch, dev, stream, src, dst, so, do, m, n,
                                  row_ptr, col, val, ws_c, ws_s, x, y, flush)
+    if compare is not None:
+        # the whole pipeline on each order (Sec. 5.6): what a user pays to go
+        # from the edge list to spmv_iters products, and how many products it
+        # takes for the reorder to pay for itself
+        r, o, it = compare["random"], compare["boba"], args.spmv_iters
+        gain = r["spmv_ms"] - o["spmv_ms"]
+        compare["pipeline"] = {
+            "spmv_iters": it,
+            "random_csr_spmv_ms": round(r["csr_ms"] + it * r["spmv_ms"], 3),
+            "boba_reorder_csr_spmv_ms": round(reorder_ms + o["csr_ms"] + it * o["spmv_ms"], 3),
+            "break_even_spmv_iters": (round((reorder_ms + o["csr_ms"] - r["csr_ms"]) / gain, 1)
+                                      if gain > 0 else None)}
     full = 24 * m + 4 * n
     reorder_roof = {"alg_bytes": full, "achieved_gbs": round(full / (reorder_ms * 1e-3) / 1e9, 1),
                     "frac": round(full / (reorder_ms * 1e-3) / 1e9 / hbm, 4),
