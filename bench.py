@@ -84,6 +84,11 @@ def algorithmic_bytes(m: int, n: int, nnz: int):
     counted once where they are produced or consumed for the first time.
     """
     bitmap = (2 * m + 7) // 8
+    bits = max(1, (n - 1).bit_length())
+    passes = (bits + 7) // 8
+    # radix passes: keys and values in and out (16m); the last one writes no
+    # keys but val and the row ends (12m + 4n); mean over the passes of a build
+    pass_mean = ((passes - 1) * 16 * m + 12 * m + 4 * n) / passes if passes > 1 else 16 * m
     return {
         "reorder.init": 4 * n + bitmap,            # write key, clear bitmap
         "reorder.first": 8 * m + 4 * n,            # stream I ++ J, final keys
@@ -92,6 +97,7 @@ def algorithmic_bytes(m: int, n: int, nnz: int):
         "reorder.emit": 4 * n + 4 * n + 4 * n,     # keys in, label + perm out
         "reorder.relabel": 16 * m + 4 * n,         # src,dst in; src_out,dst_out out; label
         "csr.hist": 4 * m,                         # read dst (outdeg is counted in pass 0)
+        "csr.pass": int(pass_mean),
         "spmv": 8 * nnz + 16 * n,
     }
 
