@@ -218,7 +218,9 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
     uint32_t *const s_vals = s_stage + TILE;
     __shared__ uint16_t s_wcnt[WARPS][256];      // per-warp digit counts, then warp prefixes
     __shared__ uint32_t s_tpre[256];              // tile-local exclusive digit offsets
-    __shared__ uint32_t s_base[256];              // global start of this tile's run of digit d
+    // global start of this tile's run of digit d minus its tile-local start:
+    // sorted tile slot j of digit d goes to s_off[d] + j (mod 2^32)
+    __shared__ uint32_t s_off[256];
     constexpr int NBIN = RANK == kRankOr ? 257 : 1;   // digits and the invalid tail
     __shared__ uint32_t s_bins[RANK == kRankOr ? WARPS : 1][NBIN];
     __shared__ typename BlockScan<BLOCK>::Smem sm;
@@ -237,6 +239,10 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
     // items of this tile; tile-local indices and global positions fit 32 bits
     // (m < 2^31)
     const int valid_n = (m - t0) < TILE ? (int)(m - t0) : TILE;
+    // every tile but the last is full; the reduce-then-scan shapes rank a
+    // full tile without the valid/invalid split (in the look-back shapes it
+    // costs registers and measured nothing)
+    const bool full = PRESCAN && valid_n == TILE;
     const uint32_t *kin_t = kin + t0, *vin_t = vin + t0;
 
     // load: item (warp, k, lane) is tile index warp*WARP_ITEMS + k*32 + lane, so
@@ -267,7 +273,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
     const uint32_t lt = (1u << lane) - 1u;
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
-        const bool valid = warp * WARP_ITEMS + k * 32 + lane < valid_n;
+        const bool valid = full || warp * WARP_ITEMS + k * 32 + lane < valid_n;
         const uint32_t d = valid ? ((key[k] >> shift) & 255u) : 256u;
         unsigned peers;
         if constexpr (RANK == kRankOr) {
@@ -277,8 +283,12 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
         } else if constexpr (RANK == kRankBallot) {
             // lanes with the same digit: intersect 8 bit-ballots (and the
             // valid/invalid split) instead of one match instruction
-            const unsigned vm = __ballot_sync(kFull, valid);
-            peers = valid ? vm : ~vm;
+            if (full) {
+                peers = kFull;
+            } else {
+                const unsigned vm = __ballot_sync(kFull, valid);
+                peers = valid ? vm : ~vm;
+            }
 #pragma unroll
             for (int b = 0; b < 8; ++b) {
                 const unsigned bm = __ballot_sync(kFull, (d >> b) & 1u);
@@ -319,14 +329,14 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
     const uint32_t tpre = BlockScan<BLOCK>::exclusive(cnt, &tot, sm);
     if (d < 256 && PRESCAN) {
         s_tpre[d] = tpre;
-        s_base[d] = tile_base[tile * 256 + d];
+        s_off[d] = tile_base[tile * 256 + d] - tpre;
     } else if (d < 256) {
         s_tpre[d] = tpre;
         // per-digit look-back across tiles, reading 8 predecessors per round trip
         uint64_t *st = status_lb + tile * 256 + d;
         if (tile == 0) {
             st_relaxed_u64(st, pass_flag(p, true) | cnt);
-            s_base[d] = dstart[digit * 256 + d];
+            s_off[d] = dstart[digit * 256 + d] - tpre;
         } else {
             st_relaxed_u64(st, pass_flag(p, false) | cnt);
             const uint64_t fa = pass_flag(p, false), fp = pass_flag(p, true);
@@ -363,7 +373,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
                 }
             }
             st_relaxed_u64(st, fp | ((excl + cnt) & kPassValMask));
-            s_base[d] = dstart[digit * 256 + d] + (uint32_t)excl;
+            s_off[d] = dstart[digit * 256 + d] + (uint32_t)excl - tpre;
         }
     }
     __syncthreads();
@@ -386,7 +396,7 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
             const uint32_t kk = s_keys[j];
             const uint32_t vv = s_vals[j];
             const uint32_t dd = (kk >> shift) & 255u;
-            const uint32_t g = s_base[dd] + (uint32_t)(j - (int)s_tpre[dd]);
+            const uint32_t g = s_off[dd] + (uint32_t)j;
             __stcs(vout + g, vv);
             if (ends == nullptr) {
                 __stcs(kout + g, kk);
