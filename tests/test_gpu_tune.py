@@ -113,3 +113,25 @@ def test_csr_ranking_variants_bit_identical(boba):
     ch = boba.tune_csr(torch.from_numpy(I).cuda(), torch.from_numpy(J).cuda(), n, reps=2)
     assert ch["csr"] in CSR_RANKINGS
     boba.tune_reset()
+
+
+@pytest.mark.parametrize("n,m", [(1, 1_000), (256, 70_001), (257, 70_001), (65_537, 300_007),
+                                 (200, (1 << 22) + 77)])
+def test_csr_variants_across_pass_counts(boba, n, m):
+    """Every radix variant on one pass (n <= 256: the run ends are found after
+    the sort), two and three passes, and a tiny n under many edges (the
+    reduce-then-scan default with a single pass), ragged m throughout."""
+    rng = np.random.default_rng(n + m)
+    I = rng.integers(0, n, m, dtype=np.int32)
+    J = np.where(rng.random(m) < 0.3, n - 1, rng.integers(0, n, m)).astype(np.int32)
+    orp, ocol, oval = oracle.coo_to_csr(I, J, n)
+    src, dst = torch.from_numpy(I).cuda(), torch.from_numpy(J).cuda()
+    for v in CSR_RANKINGS:
+        boba.load().boba_tune_set(boba.TUNE_CSR, m, v)
+        rp, col, val = boba.coo_to_csr(src, dst, n)
+        boba.stream_status()
+        np.testing.assert_array_equal(rp.cpu().numpy(), orp, err_msg=f"variant {v}")
+        np.testing.assert_array_equal(col.cpu().numpy(), ocol, err_msg=f"variant {v}")
+        np.testing.assert_array_equal(val.cpu().numpy().view(np.uint32), oval.view(np.uint32),
+                                      err_msg=f"variant {v}")
+    boba.load().boba_tune_set(boba.TUNE_CSR, m, -1)
