@@ -122,8 +122,12 @@ boba_status_t boba_reorder_ex(const int32_t *src, const int32_t *dst, int64_t m,
  *               [0, n): BOBA_ERR_ID_OUT_OF_RANGE; a look-back wait that gave
  *               up: BOBA_ERR_TIMEOUT); the caller clears it.  These errors are
  *               not reported by boba_stream_status().  With NULL they are not
- *               reported at all; an out-of-range ID still shows as -1 in
- *               src_out/dst_out.
+ *               reported at all: an out-of-range ID still shows as -1 in
+ *               src_out/dst_out, but a look-back wait that gave up leaves a
+ *               wrong perm and wrong labels with no sign of it.  Callers that
+ *               need to know pass a word.
+ * With m = 0, src, dst, src_out and dst_out may be NULL (perm_out is the
+ * identity).
  * Limits: m <= 2^22 edges and n <= 2^20 vertices; larger graphs return
  * BOBA_ERR_TOO_LARGE before anything is launched.
  * The first call on a device sets up that device (it looks up the device
@@ -329,7 +333,13 @@ boba_status_t boba_server_drain(boba_server_t *server);
  * boba_server_stats -- out[0] p50 latency (ms), out[1] p99 latency (ms),
  * out[2] throughput (Gedges/s over first arrival .. last completion),
  * out[3] requests done, out[4] edges done, out[5] peak pool bytes in use,
- * out[6] seconds spanned.  cap >= 7; returns 7.
+ * out[6] seconds spanned.  cap >= 7; returns 7.  With cap >= 13 also, and
+ * returns 13: out[7] the most requests admitted at once, out[8] requests
+ * admitted while others were still active (continuous batching), out[9] the
+ * most requests whose device work overlapped in time (from events on their
+ * streams), out[10] / out[11] p50 / p99 of the time from arrival to admission
+ * (queueing, ms), out[12] p99 of the time from admission to completion
+ * (service, ms).
  */
 int boba_server_stats(boba_server_t *server, double *out, int cap);
 
@@ -470,6 +480,34 @@ boba_status_t boba_stream_status(void *stream);
  */
 boba_status_t boba_selftest_wait_timeout(uint64_t timeout_ns, void *scratch, void *stream);
 
+/*
+ * boba_probe_gather -- a measurement aid (no step of the method): random
+ * 4-byte loads at the rate this GPU sustains, the ceiling of a pass that looks
+ * up one entry of an n-sized array per endpoint at a random index, as the
+ * first-occurrence pass (Alg. 2, Sec. 4.4) and the relabel (Sec. 5.3) do on a
+ * randomly labelled graph.  Each of a persistent grid of 256-thread blocks
+ * issues loads_per_thread loads per thread at indices from a hash of a
+ * per-thread counter, masked to the table.
+ *   mode 0  from `table` in global memory (table_words words, read only)
+ *   mode 1  from a copy of the first table_words words in each block's shared
+ *           memory (table_words * 4 <= 227 KB)
+ *   mode 2  from the distributed shared memory of clusters of `cluster` blocks
+ *           (2, 4, 8 or 16), each block holding table_words / cluster words of
+ *           the table; every load picks a block of its cluster
+ *   table_words        a power of two; `table` holds at least that many words
+ *   loads_per_thread   a positive multiple of 8
+ *   out                uint32[out_words] (device): one sum per thread, written
+ *                      so that the loads are not optimised away; the grid is
+ *                      capped at out_words / 256 blocks
+ *   loads_issued       HOST int64: the number of loads the launch issues
+ * Asynchronous; time it with events on `stream`.  Returns
+ * BOBA_ERR_INVALID_ARG for sizes outside these bounds or a cluster shape the
+ * device cannot run.  (The paper has no counterpart.)
+ */
+boba_status_t boba_probe_gather(int mode, const uint32_t *table, int64_t table_words,
+                                int64_t loads_per_thread, int cluster, uint32_t *out,
+                                int64_t out_words, int64_t *loads_issued, void *stream);
+
 /* boba_status_string -- a static, human-readable name for a status code. */
 const char *boba_status_string(boba_status_t status);
 
@@ -485,8 +523,14 @@ enum { BOBA_TUNE_FIRST = 0, BOBA_TUNE_RELABEL = 1, BOBA_TUNE_BATCHED = 2, BOBA_T
        BOBA_TUNE_CSR = 4 };
 
 /*
- * boba_tune_reorder -- times every variant (block size x loads in flight) of
- * the first-occurrence kernel, then of the relabel kernel, on this graph with
+ * boba_tune_reorder -- times every variant of the first-occurrence kernel,
+ * then of the relabel kernel (0..5: block size x loads in flight; 6: lanes of
+ * a warp holding the same ID look it up once (warp-aggregated AtomicMin, and
+ * one label gather shuffled to the group); 7: the key or label array held
+ * persisting in L2 for the launch through an access-policy window, returned
+ * to normal by the next kernel that reads it -- this variant raises the
+ * process's persisting-L2 limit to the device maximum when it first runs), on
+ * this graph with
  * boba_reorder_ex's arguments, discards any variant whose perm/src_out/dst_out
  * differ from the default's in a single bit, and keeps the fastest for graphs
  * in the same power-of-two size class of m on this device.  chosen (int[2],
@@ -513,9 +557,12 @@ boba_status_t boba_tune_batched(const int32_t *src, const int32_t *dst, const in
  * boba_tune_spmv -- the same for boba_spmv_csr (variant 0: lanes per row
  * chosen from nnz / n_rows; 1..4: 4, 8, 16, 32 lanes per row; 5..8: merge-path
  * decomposition over row ends and nonzeros with 256x8, 256x12, 512x8, 128x16
- * threads x items per tile), keyed by nnz.  The variants sum
- * in different orders, so their results may differ in the last bits; each is
- * deterministic.
+ * threads x items per tile; 9..13: merge path with a 64 KB or 32 KB cap on the
+ * shared-memory carve-out, leaving the rest to L1 for the x gathers), keyed
+ * by nnz.  The variants sum in different orders, so their results may differ
+ * in the last bits; each is deterministic.  A variant whose y is further than
+ * 1e-5 (relative L2) from variant 0's is never chosen.  Allocates a reference
+ * copy of y with cudaMalloc.
  */
 boba_status_t boba_tune_spmv(const int64_t *row_ptr, const int32_t *col, const float *val,
                              const float *x, float *y, int64_t n_rows, int64_t nnz, void *ws,

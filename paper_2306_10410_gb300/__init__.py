@@ -242,6 +242,15 @@ def boba_selftest_wait_timeout(timeout_ns, scratch, stream=None):
     return load().boba_selftest_wait_timeout(int(timeout_ns), _p(scratch), _s(stream))
 
 
+def boba_probe_gather(mode, table, table_words, loads_per_thread, cluster, out, out_words,
+                      loads_issued, stream=None):
+    """loads_issued is a ctypes c_int64 (host), passed by reference."""
+    import ctypes
+    return load().boba_probe_gather(int(mode), _p(table), table_words, loads_per_thread,
+                                    int(cluster), _p(out), out_words, ctypes.byref(loads_issued),
+                                    _s(stream))
+
+
 def boba_stream_status(stream=None):
     return load().boba_stream_status(_s(stream))
 

@@ -58,6 +58,7 @@ SIGNATURES = {
     "boba_nbr_workspace_bytes": (_SZ, [_I64, _I64]),
     "boba_stream_status": (_ST, [_P]),
     "boba_selftest_wait_timeout": (_ST, [ctypes.c_uint64, _P, _P]),
+    "boba_probe_gather": (_ST, [ctypes.c_int, _P, _I64, _I64, ctypes.c_int, _P, _I64, _P, _P]),
     "boba_status_string": (ctypes.c_char_p, [_ST]),
     "boba_version": (ctypes.c_char_p, []),
     "boba_server_create": (_P, [_SZ, ctypes.c_int, ctypes.c_int, ctypes.c_int]),

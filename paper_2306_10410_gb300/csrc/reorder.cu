@@ -15,7 +15,9 @@
 // iff position i of I ++ J is the first occurrence of its vertex, which is the
 // flag key[I[i]] == i of the method, built from the n keys instead of a second
 // pass over the 2m positions.
+#include <algorithm>
 #include <cstdio>
+#include <mutex>
 
 #include "common.cuh"
 #include "host.hpp"
@@ -49,7 +51,11 @@ __global__ void __launch_bounds__(256) k_init(uint32_t *__restrict__ key, int64_
 // read most earlier positions are already recorded and the filtering read
 // (key[v] <= i) skips the atomic.
 // ---------------------------------------------------------------------------
-template <bool VEC, int BLOCK, int U, bool ATOMIC = true>
+// With AGG the lanes of a warp first group equal IDs of the same slot of their
+// int4 rounds (__match_any_sync); only the lowest lane of a group, which holds
+// the group's lowest position, reads and updates the key (warp-aggregated
+// AtomicMin).  The result is the same: the other positions are higher.
+template <bool VEC, int BLOCK, int U, bool ATOMIC = true, bool AGG = false>
 __device__ __forceinline__ void first_body(const int32_t *__restrict__ src,
                                                        const int32_t *__restrict__ dst, int64_t m,
                                                        uint32_t n, uint32_t *key, uint32_t *status,
@@ -79,12 +85,21 @@ __device__ __forceinline__ void first_body(const int32_t *__restrict__ src,
                 }
             }
             uint32_t cur[U][4];
+            bool lead[U][4];
 #pragma unroll
             for (int u = 0; u < U; ++u)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int32_t v = comp(q[u], j);
-                    cur[u][j] = (ok[u] && (uint32_t)v < n) ? key[v] : 0u;
+                    const bool valid = ok[u] && (uint32_t)v < n;
+                    lead[u][j] = true;
+                    if constexpr (AGG) {
+                        // IDs are < 2^31; an invalid slot gets a value of its own
+                        const uint32_t tag = valid ? (uint32_t)v : (0x80000000u | (threadIdx.x & 31));
+                        const unsigned grp = __match_any_sync(kFull, tag);
+                        lead[u][j] = (__ffs(grp) - 1) == (int)(threadIdx.x & 31);
+                    }
+                    cur[u][j] = (valid && lead[u][j]) ? key[v] : 0u;
                 }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -93,7 +108,7 @@ __device__ __forceinline__ void first_body(const int32_t *__restrict__ src,
                 for (int j = 0; j < 4; ++j) {
                     const int32_t v = comp(q[u], j);
                     if ((uint32_t)v >= n) raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE);
-                    else first_update<ATOMIC>(v, p0[u] + (uint32_t)j, cur[u][j], key);
+                    else if (lead[u][j]) first_update<ATOMIC>(v, p0[u] + (uint32_t)j, cur[u][j], key);
                 }
             }
         }
@@ -174,12 +189,12 @@ __global__ void __launch_bounds__(256) k_first_interleaved(const int32_t *__rest
 }
 
 // Variants for the autotuner (vector path): BLOCK threads, U int4 loads in flight.
-template <int BLOCK, int U>
+template <int BLOCK, int U, bool AGG = false>
 __global__ void __launch_bounds__(BLOCK) k_first_v(const int32_t *__restrict__ src,
                                                    const int32_t *__restrict__ dst, int64_t m,
                                                    uint32_t n, uint32_t *key, uint32_t *status)
 {
-    first_body<true, BLOCK, U>(src, dst, m, n, key, status, 0, m);
+    first_body<true, BLOCK, U, true, AGG>(src, dst, m, n, key, status, 0, m);
 }
 
 // ---------------------------------------------------------------------------
@@ -340,7 +355,10 @@ __global__ void __launch_bounds__(kEmitBlock) k_emit(const uint32_t *__restrict_
 // kept.  src_out/dst_out may alias src/dst: each element is read before the
 // same thread writes it.
 // ---------------------------------------------------------------------------
-template <bool VEC, int BLOCK, int U>
+// With AGG the lanes of a warp group equal IDs of the same slot of their int4
+// rounds; the lowest lane of a group gathers the label and shuffles it to the
+// others.
+template <bool VEC, int BLOCK, int U, bool AGG = false>
 __device__ __forceinline__ void relabel_body(const int32_t *src, const int32_t *dst,
                                                            int64_t m, uint32_t n,
                                                            const int32_t *__restrict__ label,
@@ -360,12 +378,32 @@ __device__ __forceinline__ void relabel_body(const int32_t *src, const int32_t *
                 if (g < total) {
                     const bool hi = g >= Q;
                     q[u] = ld_stream(reinterpret_cast<const int4 *>(hi ? dst : src) + (hi ? g - Q : g));
+                } else if constexpr (AGG) {
+                    q[u] = make_int4(0, 0, 0, 0);      // read by the match, never used
                 }
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int64_t g = base + u * BLOCK + threadIdx.x;
-                if (g < total) {
+                if constexpr (AGG) {
+                    // every lane takes part in the match and the shuffle
+                    int4 r;
+                    int32_t *rr = &r.x;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int32_t v = comp(q[u], j);
+                        const bool valid = g < total && (uint32_t)v < n;
+                        const uint32_t tag = valid ? (uint32_t)v : (0x80000000u | (threadIdx.x & 31));
+                        const unsigned grp = __match_any_sync(kFull, tag);
+                        const int leader = __ffs(grp) - 1;
+                        int32_t x = -1;
+                        if (valid && leader == (int)(threadIdx.x & 31)) x = __ldg(label + v);
+                        x = __shfl_sync(kFull, x, leader);
+                        rr[j] = valid ? x : -1;
+                        if (g < total && !valid) raise_status(status, BOBA_ERR_ID_OUT_OF_RANGE);
+                    }
+                    if (g < total) q[u] = r;
+                } else if (g < total) {
                     int4 r;
                     int32_t *rr = &r.x;
 #pragma unroll
@@ -410,37 +448,152 @@ __global__ void __launch_bounds__(kRelabelBlock) k_relabel(const int32_t *src, c
     relabel_body<VEC, kRelabelBlock, kRelabelUnroll>(src, dst, m, n, label, src_out, dst_out, status);
 }
 
-template <int BLOCK, int U>
+template <int BLOCK, int U, bool AGG = false>
 __global__ void __launch_bounds__(BLOCK) k_relabel_v(const int32_t *src, const int32_t *dst,
                                                      int64_t m, uint32_t n,
                                                      const int32_t *__restrict__ label,
                                                      int32_t *src_out, int32_t *dst_out,
                                                      uint32_t *status)
 {
-    relabel_body<true, BLOCK, U>(src, dst, m, n, label, src_out, dst_out, status);
+    relabel_body<true, BLOCK, U, AGG>(src, dst, m, n, label, src_out, dst_out, status);
 }
 
 // Launch one tuned variant of the vector-path first-occurrence / relabel kernel.
-template <int BLOCK, int U>
+template <int BLOCK, int U, bool AGG = false>
 void launch_first_v(const ReorderArgs &a, cudaStream_t stream)
 {
     const int64_t work = cdiv(2 * a.m, 4LL * BLOCK * U);
-    const int g = persistent_grid((const void *)k_first_v<BLOCK, U>, BLOCK, work);
+    const int g = persistent_grid((const void *)k_first_v<BLOCK, U, AGG>, BLOCK, work);
     BOBA_TIMED("reorder.first", stream,
-               k_first_v<BLOCK, U><<<g, BLOCK, 0, stream>>>(a.src, a.dst, a.m, a.n, a.key, a.status));
+               k_first_v<BLOCK, U, AGG><<<g, BLOCK, 0, stream>>>(a.src, a.dst, a.m, a.n, a.key,
+                                                                a.status));
 }
 
-template <int BLOCK, int U>
+template <int BLOCK, int U, bool AGG = false>
 void launch_relabel_v(const ReorderArgs &a, cudaStream_t stream)
 {
     const int64_t work = cdiv(2 * a.m, 4LL * BLOCK * U);
-    const int g = persistent_grid((const void *)k_relabel_v<BLOCK, U>, BLOCK, work);
+    const int g = persistent_grid((const void *)k_relabel_v<BLOCK, U, AGG>, BLOCK, work);
     BOBA_TIMED("reorder.relabel", stream,
-               k_relabel_v<BLOCK, U><<<g, BLOCK, 0, stream>>>(a.src, a.dst, a.m, a.n, a.label,
-                                                              a.src_out, a.dst_out, a.status));
+               k_relabel_v<BLOCK, U, AGG><<<g, BLOCK, 0, stream>>>(a.src, a.dst, a.m, a.n, a.label,
+                                                                  a.src_out, a.dst_out, a.status));
 }
 
-// Variant table: index -> (block, loads in flight).  Index 0 is the default.
+// ---------------------------------------------------------------------------
+// L2 residency of the looked-up array (variant 7 of both lookup kernels): the
+// launch carries an access-policy window over the key (or label) array with
+// hits marked persisting and the rest streaming, so the n-sized array keeps
+// its L2 lines against the edge streams.  The lines are set back to normal by
+// the next kernel that reads the whole array (k_mark for the keys, k_touch for
+// the labels) under a window marked normal, so later work (the CSR build)
+// gets the whole L2 back.  The process's persisting-L2 limit is raised to the
+// device maximum once per device when this variant first runs.
+// ---------------------------------------------------------------------------
+struct L2Window {
+    bool ok = false;
+    size_t max_window = 0, limit = 0;
+};
+
+const L2Window &l2_window_info()
+{
+    static std::mutex mu;
+    static L2Window info[64];
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    dev &= 63;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done[dev]) {
+        done[dev] = true;
+        int maxw = 0, maxp = 0;
+        if (cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev) == cudaSuccess &&
+            maxw > 0 && maxp > 0 &&
+            cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)maxp) == cudaSuccess) {
+            info[dev].ok = true;
+            info[dev].max_window = (size_t)maxw;
+            info[dev].limit = (size_t)maxp;
+        } else {
+            (void)cudaGetLastError();
+        }
+    }
+    return info[dev];
+}
+
+// Launch `kern` with an access-policy window over [base, base + bytes).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_windowed(void (*kern)(KArgs...), int grid, int block, cudaStream_t stream,
+                            const void *base, size_t bytes, cudaAccessProperty hit,
+                            Args... args)
+{
+    const L2Window &w = l2_window_info();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    if (w.ok && bytes > 0) {
+        const size_t nb = bytes < w.max_window ? bytes : w.max_window;
+        attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[0].val.accessPolicyWindow.base_ptr = const_cast<void *>(base);
+        attr[0].val.accessPolicyWindow.num_bytes = nb;
+        attr[0].val.accessPolicyWindow.hitRatio =
+            hit == cudaAccessPropertyPersisting ? (float)std::min(1.0, (double)w.limit / (double)nb)
+                                                : 1.0f;
+        attr[0].val.accessPolicyWindow.hitProp = hit;
+        attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// Reads every label once under a window marked normal (see above).
+__global__ void __launch_bounds__(256) k_touch(const int32_t *__restrict__ a, int64_t n,
+                                               uint32_t *sink)
+{
+    uint32_t acc = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        acc ^= (uint32_t)a[i];
+    if (acc == 0x9E3779B9u) atomicAdd(sink, 1u);      // keeps the loads; almost never taken
+}
+
+void launch_first_windowed(const ReorderArgs &a, cudaStream_t stream)
+{
+    constexpr int B = 256, U = 4;
+    const int64_t work = cdiv(2 * a.m, 4LL * B * U);
+    const int g = persistent_grid((const void *)k_first_v<B, U>, B, work);
+    cudaError_t e = cudaSuccess;
+    BOBA_TIMED("reorder.first", stream,
+               e = launch_windowed(k_first_v<B, U, false>, g, B, stream, a.key, (size_t)a.n * 4,
+                                   cudaAccessPropertyPersisting, a.src, a.dst, a.m, a.n, a.key,
+                                   a.status));
+    (void)e;
+}
+
+void launch_relabel_windowed(const ReorderArgs &a, cudaStream_t stream)
+{
+    constexpr int B = 256, U = 4;
+    const int64_t work = cdiv(2 * a.m, 4LL * B * U);
+    const int g = persistent_grid((const void *)k_relabel_v<B, U>, B, work);
+    cudaError_t e = cudaSuccess;
+    BOBA_TIMED("reorder.relabel", stream,
+               e = launch_windowed(k_relabel_v<B, U, false>, g, B, stream, a.label,
+                                   (size_t)a.n * 4, cudaAccessPropertyPersisting, a.src, a.dst,
+                                   a.m, a.n, (const int32_t *)a.label, a.src_out, a.dst_out,
+                                   a.status));
+    const int gt = persistent_grid((const void *)k_touch, 256, cdiv(a.n, 256));
+    BOBA_TIMED("reorder.relabel.reset", stream,
+               e = launch_windowed(k_touch, gt, 256, stream, a.label, (size_t)a.n * 4,
+                                   cudaAccessPropertyNormal, (const int32_t *)a.label,
+                                   (int64_t)a.n, a.counters + kCtrScratch));
+    (void)e;
+}
+
+// Variant table: index -> (block, loads in flight); 6 is the warp-aggregated
+// form of the default shape, 7 the default shape with the looked-up array
+// held persisting in L2.  Index 0 is the default.
 bool launch_first_variant(int v, const ReorderArgs &a, cudaStream_t s)
 {
     switch (v) {
@@ -449,6 +602,8 @@ bool launch_first_variant(int v, const ReorderArgs &a, cudaStream_t s)
     case 3: launch_first_v<512, 4>(a, s); return true;
     case 4: launch_first_v<128, 8>(a, s); return true;
     case 5: launch_first_v<512, 2>(a, s); return true;
+    case 6: launch_first_v<256, 4, true>(a, s); return true;
+    case 7: launch_first_windowed(a, s); return true;
     default: return false;
     }
 }
@@ -461,6 +616,8 @@ bool launch_relabel_variant(int v, const ReorderArgs &a, cudaStream_t s)
     case 3: launch_relabel_v<512, 4>(a, s); return true;
     case 4: launch_relabel_v<128, 8>(a, s); return true;
     case 5: launch_relabel_v<512, 2>(a, s); return true;
+    case 6: launch_relabel_v<256, 4, true>(a, s); return true;
+    case 7: launch_relabel_windowed(a, s); return true;
     default: return false;
     }
 }
@@ -482,6 +639,7 @@ template __global__ void k_relabel<false>(const int32_t *, const int32_t *, int6
 boba_status_t launch_reorder(const ReorderArgs &a, int64_t n4, size_t nzero_u32,
                              cudaStream_t stream)
 {
+    bool first_windowed = false;
     {
         const int64_t work = cdiv((int64_t)((size_t)n4 > nzero_u32 ? (size_t)n4 : nzero_u32) / 4, 256);
         const int g = persistent_grid((const void *)k_init, 256, work);
@@ -509,6 +667,7 @@ boba_status_t launch_reorder(const ReorderArgs &a, int64_t n4, size_t nzero_u32,
     } else if (a.m > 0) {
         const bool vec = aligned16(a.src) && aligned16(a.dst);
         const int64_t work = cdiv(2 * a.m, 4 * kFirstBlock * kFirstUnroll);
+        first_windowed = vec && tuned_variant(kTuneFirst, a.m) == 7;
         if (vec && launch_first_variant(tuned_variant(kTuneFirst, a.m), a, stream)) {
             // tuned variant launched
         } else if (vec) {
@@ -525,7 +684,18 @@ boba_status_t launch_reorder(const ReorderArgs &a, int64_t n4, size_t nzero_u32,
     }
     if (a.m > 0) {
         const int gm = persistent_grid((const void *)k_mark, 256, cdiv(n4 / 4, 256));
-        BOBA_TIMED("reorder.mark", stream, k_mark<<<gm, 256, 0, stream>>>(a.key, n4, a.bitmap));
+        if (first_windowed) {
+            // k_mark reads every key: under a normal window it returns the
+            // persisting key lines to normal
+            cudaError_t e = cudaSuccess;
+            BOBA_TIMED("reorder.mark", stream,
+                       e = launch_windowed(k_mark, gm, 256, stream, a.key, (size_t)a.n * 4,
+                                           cudaAccessPropertyNormal, (const uint32_t *)a.key, n4,
+                                           a.bitmap));
+            BOBA_CUDA_TRY(e);
+        } else {
+            BOBA_TIMED("reorder.mark", stream, k_mark<<<gm, 256, 0, stream>>>(a.key, n4, a.bitmap));
+        }
         BOBA_TIMED("reorder.scan", stream,
                    k_scan<<<(unsigned)a.scan_tiles, kScanBlock, 0, stream>>>(
                        a.bitmap, a.grp, a.tstat_scan, a.counters, a.scan_tiles, a.status));

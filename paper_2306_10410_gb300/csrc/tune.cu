@@ -1,15 +1,18 @@
 // Autotuner: for each kernel family with several correct launch variants
 // (block size and loads in flight of the first-occurrence and relabel
-// streams, the schedule of the batched path, the SpMV kernel and shape --
+// streams, their warp-aggregated and L2-persisting forms, the schedule of the
+// batched path, the SpMV kernel and shape --
 // lanes per row, or merge-path block, items and shared-memory carve-out --
 // and the ranking, tile shape and offset scheme (look-back or
 // reduce-then-scan) of the radix passes), time every variant on the caller's
 // data and keep the fastest for that size class (log2 of the size) on this
 // device.  Integer results must equal the default's bit for bit (a variant
 // that differs is skipped); the SpMV shapes differ only in the order of fp32
-// sums, each within the error bound.  Choices can be saved to and loaded from
+// sums, and one whose product is further than the error bound (relative L2
+// 1e-5) from the default's is skipped too.  Choices can be saved to and loaded from
 // a text file keyed by GPU name.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -25,8 +28,11 @@ namespace boba {
 namespace {
 
 constexpr int kClasses = 64;
+// The fp32 SpMV is within 1e-5 (relative L2) of the fp64 product; a tuned
+// variant must also stay within that of the default variant's fp32 result.
+constexpr double kSpmvTuneRelL2 = 1e-5;
 constexpr int kMaxDev = 64;
-constexpr int kVariants[kTuneKernels] = {6, 6, 6, 14, 10};   // first, relabel, batched, spmv, csr
+constexpr int kVariants[kTuneKernels] = {8, 8, 6, 14, 10};   // first, relabel, batched, spmv, csr
 const char *kNames[kTuneKernels] = {"first", "relabel", "batched", "spmv", "csr"};
 
 std::mutex g_tmu;
@@ -89,6 +95,36 @@ int64_t count_diff(const void *a, const void *b, int64_t words, unsigned long lo
         return -1;
     }
     return (int64_t)h;
+}
+
+// sums[0] += (a - b)^2, sums[1] += b^2 over n floats, in fp64.
+__global__ void k_sq_diff(const float *a, const float *b, int64_t n, double *sums)
+{
+    double d2 = 0.0, b2 = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = (double)a[i] - (double)b[i];
+        d2 += d * d;
+        b2 += (double)b[i] * (double)b[i];
+    }
+    if (d2 != 0.0) atomicAdd(&sums[0], d2);
+    if (b2 != 0.0) atomicAdd(&sums[1], b2);
+}
+
+// Relative L2 distance ||a - b|| / ||b|| of two device float arrays (-1 on a
+// CUDA error; ||a|| if b is all zero).
+double rel_l2(const float *a, const float *b, int64_t n, double *dsums, cudaStream_t s)
+{
+    if (n <= 0) return 0.0;
+    cudaMemsetAsync(dsums, 0, 2 * sizeof(double), s);
+    k_sq_diff<<<256, 256, 0, s>>>(a, b, n, dsums);
+    double h[2] = {0.0, 0.0};
+    cudaMemcpyAsync(h, dsums, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return -1.0;
+    }
+    return h[1] > 0.0 ? sqrt(h[0] / h[1]) : sqrt(h[0]);
 }
 
 template <class F>
@@ -272,6 +308,16 @@ extern "C" boba_status_t boba_tune_spmv(const int64_t *row_ptr, const int32_t *c
     if (reps < 1 || n_rows <= 0) return BOBA_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream_);
     const int cls = size_class(nnz);
+    // variant 0's product is the reference: a variant further than
+    // kSpmvTuneRelL2 from it (relative L2) is never chosen
+    float *ref = nullptr;
+    double *dsums = nullptr;
+    if (cudaMalloc(&ref, (size_t)n_rows * 4) != cudaSuccess ||
+        cudaMalloc(&dsums, 2 * sizeof(double)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        if (ref) cudaFree(ref);
+        return BOBA_ERR_CUDA;
+    }
     int best = 0;
     double best_ms = 1e30;
     boba_status_t st = BOBA_OK;
@@ -279,11 +325,19 @@ extern "C" boba_status_t boba_tune_spmv(const int64_t *row_ptr, const int32_t *c
         set_entry(kTuneSpmv, cls, v);
         auto run = [&] { return boba_spmv_csr(row_ptr, col, val, x, y, n_rows, nnz, ws, ws_bytes, s); };
         if ((st = run()) != BOBA_OK) break;
+        if (v == 0) {
+            cudaMemcpyAsync(ref, y, (size_t)n_rows * 4, cudaMemcpyDeviceToDevice, s);
+        } else {
+            const double e = rel_l2(y, ref, n_rows, dsums, s);
+            if (e < 0.0 || e > kSpmvTuneRelL2) continue;
+        }
         const double t = time_ms(run, reps, s);
         if (t < best_ms) { best_ms = t; best = v; }
     }
     set_entry(kTuneSpmv, cls, best);
     if (chosen) chosen[0] = best;
+    cudaFree(ref);
+    cudaFree(dsums);
     if (cudaGetLastError() != cudaSuccess) return BOBA_ERR_CUDA;
     return st;
 }

@@ -146,7 +146,12 @@ def test_full_size_rmat24_csr_spmv(boba):
     np.testing.assert_array_equal(rp.cpu().numpy(), orp)
     np.testing.assert_array_equal(col.cpu().numpy(), ocol)
     np.testing.assert_array_equal(val.cpu().numpy().view(np.uint32), oval.view(np.uint32))
-    check_spmv(boba, (rp, col, val), (orp, ocol, oval), synth.uniform_f32(w.n, seed=w.seed))
+    x = synth.uniform_f32(w.n, seed=w.seed)
+    check_spmv(boba, (rp, col, val), (orp, ocol, oval), x)
+    # every SpMV variant -- the lanes-per-row kernels and every merge-path shape,
+    # among them the one the tuner picks for this graph -- on this CSR, within
+    # the fp32 bound of the fp64 oracle
+    check_spmv_all_variants(boba, (rp, col, val), (orp, ocol, oval), x, w.m)
     # the default above ran the reduce-then-scan passes (variant 8); the
     # look-back passes (1, 5) and the other reduce-then-scan ranking (9) too
     for v in (1, 5, 9):
@@ -160,7 +165,50 @@ def test_full_size_rmat24_csr_spmv(boba):
     boba.load().boba_tune_set(boba.TUNE_CSR, w.m, -1)
 
 
-@pytest.mark.parametrize("variant", list(range(14)))
+N_SPMV_VARIANTS = 14
+
+
+def check_spmv_all_variants(boba, gpu_csr, ora_csr, x, nnz):
+    """y of every SpMV variant against one fp64 oracle product."""
+    rp, col, val = gpu_csr
+    y64 = oracle.spmv_f64(*ora_csr, x)
+    nrm = np.linalg.norm(y64)
+    xd = dev(x)
+    errs = {}
+    try:
+        for v in range(N_SPMV_VARIANTS):
+            boba.load().boba_tune_set(boba.TUNE_SPMV, nnz, v)
+            y = boba.spmv(rp, col, val, xd)
+            boba.stream_status()
+            y32 = y.cpu().numpy().astype(np.float64)
+            errs[v] = float(np.linalg.norm(y32 - y64) / nrm)
+    finally:
+        boba.load().boba_tune_set(boba.TUNE_SPMV, nnz, -1)
+    bad = {v: e for v, e in errs.items() if not e <= SPMV_RTOL}
+    assert not bad, bad
+    return errs
+
+
+@pytest.mark.slow
+def test_full_size_rmat24_random_order_csr_spmv(boba):
+    """The same graph in its input (random) order, the baseline the benchmark
+    compares against: CSR bit-exact, every SpMV variant within 1e-5 of fp64."""
+    w = synth.RMAT24
+    I, J = w.generate()
+    src, dst = dev(I), dev(J)
+    rp, col, val = boba.coo_to_csr(src, dst, w.n)
+    boba.stream_status()
+    del src, dst
+    orp, ocol, oval = oracle.coo_to_csr(I, J, w.n)
+    del I, J
+    np.testing.assert_array_equal(rp.cpu().numpy(), orp)
+    np.testing.assert_array_equal(col.cpu().numpy(), ocol)
+    np.testing.assert_array_equal(val.cpu().numpy().view(np.uint32), oval.view(np.uint32))
+    check_spmv_all_variants(boba, (rp, col, val), (orp, ocol, oval),
+                            synth.uniform_f32(w.n, seed=w.seed), w.m)
+
+
+@pytest.mark.parametrize("variant", list(range(N_SPMV_VARIANTS)))
 @pytest.mark.parametrize("case", ["rmat14", "hubs", "empty_rows", "one_row", "no_edges"])
 def test_spmv_variants(boba, variant, case):
     """Every SpMV variant (lanes per row 4..32, merge path) within the fp32 bound,
