@@ -114,7 +114,7 @@ struct Request {
     float *y_h = nullptr;
     int32_t *perm_h = nullptr;
     int64_t m = 0, n = 0;
-    Clock::time_point arrival, done_at;
+    Clock::time_point arrival, admitted, done_at;
     std::shared_ptr<Wave> wave;
     size_t packed_e = 0, packed_v = 0;       // offsets inside the wave's packed arrays
     // per-request device arrays inside the wave block
@@ -124,6 +124,7 @@ struct Request {
     void *csr_ws = nullptr, *spmv_ws = nullptr;
     size_t csr_ws_bytes = 0, spmv_ws_bytes = 0;
     cudaStream_t stream = nullptr;
+    cudaEvent_t started = nullptr;           // its stream reached its work (after the wave's reorder)
     cudaEvent_t done = nullptr;
     boba_status_t status = BOBA_OK;
 };
@@ -174,6 +175,11 @@ struct Server {
     std::list<Request *> active;
     std::vector<Request *> finished;          // not yet returned by poll
     std::vector<double> latencies_ms;
+    std::vector<double> queue_ms, service_ms;     // arrival -> admission, admission -> done
+    std::vector<std::pair<float, float>> device_spans;   // [start, end] ms since `epoch`
+    cudaEvent_t epoch = nullptr;              // reference point of the device spans
+    size_t peak_active = 0;                   // most requests admitted at once
+    int64_t joined_busy = 0;                  // requests admitted while others were active
     int64_t next_id = 0, edges_done = 0, requests_done = 0;
     Clock::time_point first_arrival, last_done;
     bool any_arrival = false;
@@ -251,6 +257,8 @@ bool Server::launch_wave(std::vector<Request *> &rs)
         r->status = st;
         r->stream = streams[next_stream++ % streams.size()];
         cudaStreamWaitEvent(r->stream, reordered, 0);
+        cudaEventCreate(&r->started);
+        cudaEventRecord(r->started, r->stream);
         if (r->x_h) cudaMemcpyAsync(r->x, r->x_h, 4 * (size_t)r->n, cudaMemcpyHostToDevice, r->stream);
         if (st == BOBA_OK)
             st = boba_coo_to_csr(so + r->packed_e, dout + r->packed_e, r->m, r->n, r->row_ptr,
@@ -263,7 +271,7 @@ bool Server::launch_wave(std::vector<Request *> &rs)
             cudaMemcpyAsync(r->perm_h, perm + r->packed_v, 4 * (size_t)r->n, cudaMemcpyDeviceToHost,
                             r->stream);
         r->status = st;
-        cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming);
+        cudaEventCreate(&r->done);
         cudaEventRecord(r->done, r->stream);
     }
     cudaEventDestroy(reordered);     // released once its work completes
@@ -285,10 +293,21 @@ void Server::run()
                 if (q == cudaErrorNotReady) { ++it; continue; }
                 if (q != cudaSuccess) { r->status = BOBA_ERR_CUDA; (void)cudaGetLastError(); }
                 r->done_at = Clock::now();
+                float t0 = 0.f, t1 = 0.f;
+                if (cudaEventElapsedTime(&t0, epoch, r->started) == cudaSuccess &&
+                    cudaEventElapsedTime(&t1, epoch, r->done) == cudaSuccess)
+                    device_spans.emplace_back(t0, t1);
+                else
+                    (void)cudaGetLastError();
+                cudaEventDestroy(r->started);
                 cudaEventDestroy(r->done);
-                r->done = nullptr;
+                r->started = r->done = nullptr;
                 latencies_ms.push_back(
                     std::chrono::duration<double, std::milli>(r->done_at - r->arrival).count());
+                queue_ms.push_back(
+                    std::chrono::duration<double, std::milli>(r->admitted - r->arrival).count());
+                service_ms.push_back(
+                    std::chrono::duration<double, std::milli>(r->done_at - r->admitted).count());
                 edges_done += r->m;
                 requests_done += 1;
                 last_done = r->done_at;
@@ -311,7 +330,13 @@ void Server::run()
                     for (auto it = wave.rbegin(); it != wave.rend(); ++it) pending.push_front(*it);
                     wave.clear();
                 } else {
-                    for (Request *r : wave) active.push_back(r);
+                    const Clock::time_point now = Clock::now();
+                    if (!active.empty()) joined_busy += (int64_t)wave.size();
+                    for (Request *r : wave) {
+                        r->admitted = now;
+                        active.push_back(r);
+                    }
+                    peak_active = std::max(peak_active, active.size());
                 }
             }
             if (stop.load() && pending.empty() && active.empty()) break;
@@ -349,6 +374,8 @@ boba_server_t *boba_server_create(size_t hbm_budget_bytes, int max_active, int s
         S->streams.push_back(s);
     }
     cudaStreamCreateWithFlags(&S->wave_stream, cudaStreamNonBlocking);
+    cudaEventCreate(&S->epoch);
+    cudaEventRecord(S->epoch, S->wave_stream);
     S->worker = std::thread([S] { S->run(); });
     return reinterpret_cast<boba_server_t *>(S);
 }
@@ -438,13 +465,13 @@ int boba_server_stats(boba_server_t *h, double *out, int cap)
     auto *S = reinterpret_cast<Server *>(h);
     if (!S || !out || cap < 7) return -1;
     std::lock_guard<std::mutex> lk(S->mu);
-    std::vector<double> l = S->latencies_ms;
-    std::sort(l.begin(), l.end());
-    auto pct = [&](double q) {
-        if (l.empty()) return 0.0;
-        size_t i = (size_t)(q * (double)(l.size() - 1) + 0.5);
-        return l[std::min(i, l.size() - 1)];
+    auto pct_of = [](std::vector<double> v, double q) {
+        if (v.empty()) return 0.0;
+        std::sort(v.begin(), v.end());
+        size_t i = (size_t)(q * (double)(v.size() - 1) + 0.5);
+        return v[std::min(i, v.size() - 1)];
     };
+    auto pct = [&](double q) { return pct_of(S->latencies_ms, q); };
     const double span =
         S->any_arrival && S->requests_done > 0
             ? std::chrono::duration<double>(S->last_done - S->first_arrival).count()
@@ -456,7 +483,23 @@ int boba_server_stats(boba_server_t *h, double *out, int cap)
     out[4] = (double)S->edges_done;
     out[5] = (double)S->pool.peak();
     out[6] = span;
-    return 7;
+    if (cap < 13) return 7;
+    // most requests whose device work overlapped: a sweep over the spans
+    std::vector<std::pair<float, int>> ev;
+    for (const auto &sp : S->device_spans) {
+        ev.emplace_back(sp.first, 1);
+        ev.emplace_back(sp.second, -1);
+    }
+    std::sort(ev.begin(), ev.end());          // an end before a start at the same instant
+    int cur = 0, best = 0;
+    for (const auto &e : ev) best = std::max(best, cur += e.second);
+    out[7] = (double)S->peak_active;
+    out[8] = (double)S->joined_busy;
+    out[9] = (double)best;
+    out[10] = pct_of(S->queue_ms, 0.50);
+    out[11] = pct_of(S->queue_ms, 0.99);
+    out[12] = pct_of(S->service_ms, 0.99);
+    return 13;
 }
 
 void boba_server_destroy(boba_server_t *h)
@@ -470,6 +513,7 @@ void boba_server_destroy(boba_server_t *h)
     for (Request *r : S->finished) delete r;
     for (cudaStream_t s : S->streams) cudaStreamDestroy(s);
     cudaStreamDestroy(S->wave_stream);
+    cudaEventDestroy(S->epoch);
     delete S;
 }
 

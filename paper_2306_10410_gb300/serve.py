@@ -9,7 +9,9 @@ only marshals arguments and drives arrivals.
 log-uniform in [1e4, 1e8], n = m/16 rounded to a power of two for R-MAT, a
 side of about sqrt(m/4) for the grid), calibrates the mean service time with
 each graph run alone, sets the Poisson arrival rate to a target device load,
-and replays the arrivals in real time.
+and replays the arrivals in real time.  ``serve_vs_sequential`` runs a request
+list at saturation through the server and one request at a time through the
+per-graph entry points, and compares the outputs bit for bit.
 """
 from __future__ import annotations
 
@@ -70,11 +72,13 @@ class Server:
             raise BobaError(rc, "boba_server_drain")
 
     def stats(self) -> dict:
-        out = (ctypes.c_double * 8)()
-        self.lib.boba_server_stats(self.h, out, 8)
+        out = (ctypes.c_double * 13)()
+        self.lib.boba_server_stats(self.h, out, 13)
         return {"p50_ms": out[0], "p99_ms": out[1], "gedges_s": out[2],
                 "requests": int(out[3]), "edges": int(out[4]), "peak_pool_bytes": int(out[5]),
-                "span_s": out[6]}
+                "span_s": out[6], "peak_active": int(out[7]), "joined_while_busy": int(out[8]),
+                "peak_device_overlap": int(out[9]), "p50_queue_ms": out[10],
+                "p99_queue_ms": out[11], "p99_service_ms": out[12]}
 
     def close(self):
         if self.h:
@@ -143,10 +147,11 @@ def calibrate(server: Server, pool) -> list:
 
 def serve_workload(n_requests: int = 400, pool_size: int = 32, load: float = 0.8,
                    seed: int = 0xB0BA0004, budget_bytes: int = 120 << 30, spmv_iters: int = 10,
-                   max_active: int = 64, m_lo: float = 1e4, m_hi: float = 1e8):
+                   max_active: int = 64, m_lo: float = 1e4, m_hi: float = 1e8, pool=None):
     """Replay a Poisson stream of requests in real time; return the server's statistics."""
     import synth
-    pool = request_pool(pool_size, seed, m_lo, m_hi)
+    pool = request_pool(pool_size, seed, m_lo, m_hi) if pool is None else pool
+    pool_size = len(pool)
     with Server(budget_bytes, max_active, spmv_iters) as srv:
         svc = calibrate(srv, pool)
     mean_svc_s = float(np.mean(svc)) / 1e3
@@ -182,3 +187,116 @@ def serve_workload(n_requests: int = 400, pool_size: int = 32, load: float = 0.8
                "pool_edges_mean": float(np.mean([g["m"] for g in pool])),
                "spmv_iters": spmv_iters, "budget_bytes": budget_bytes})
     return st
+
+
+# ---------------------------------------------------------------------------
+# saturation: the server against one request at a time, at identical output
+# ---------------------------------------------------------------------------
+
+def request_order(n_requests: int, pool_size: int, seed: int) -> np.ndarray:
+    """Which pool graph each request of a closed-loop run uses (seeded)."""
+    import synth
+    d = synth.draws(n_requests, seed, stream=23)
+    return (d % np.uint64(pool_size)).astype(np.int64)
+
+
+def run_saturated(pool, order, budget_bytes: int = 120 << 30, spmv_iters: int = 10,
+                  max_active: int = 64):
+    """Every request submitted at once (the server is never idle): throughput at
+    saturation.  Returns (stats, ys, perms) with one host output per request."""
+    ys = [_pinned_out(pool[k]["n"]) for k in order]
+    perms = [torch.empty(pool[k]["n"], dtype=torch.int32, pin_memory=True) for k in order]
+    with Server(budget_bytes, max_active, spmv_iters) as srv:
+        g = pool[int(order[0])]                          # warm the path once
+        srv.submit(g["src"], g["dst"], g["n"], g["x"], _pinned_out(g["n"]))
+        srv.drain()
+        srv.poll()
+    with Server(budget_bytes, max_active, spmv_iters) as srv:
+        t0 = time.perf_counter()
+        for i, k in enumerate(order):
+            g = pool[int(k)]
+            srv.submit(g["src"], g["dst"], g["n"], g["x"], ys[i], perms[i])
+        srv.drain()
+        t1 = time.perf_counter()
+        done = srv.poll()
+        st = srv.stats()
+    bad = [s for _, _, s in done if s != 0]
+    if bad or len(done) != len(order):
+        raise BobaError(bad[0] if bad else 6, "saturated run")
+    edges = sum(pool[int(k)]["m"] for k in order)
+    st.update({"wall_s": t1 - t0, "gedges_s_wall": edges / (t1 - t0) / 1e9,
+               "requests_submitted": len(order)})
+    return st, ys, perms
+
+
+def run_sequential(pool, order, spmv_iters: int = 10):
+    """The same requests one after another through the per-graph entry points on
+    one stream, as a caller without the server would run them: copy the edges
+    and x in, boba_reorder_ex, boba_coo_to_csr, spmv_iters x boba_spmv_csr, copy
+    y and perm out.  Device buffers are sized once for the largest request.
+    Returns (stats, ys, perms)."""
+    from . import (boba_coo_to_csr, boba_coo_to_csr_workspace_bytes, boba_reorder_ex,
+                   boba_reorder_workspace_bytes, boba_spmv_csr, boba_spmv_workspace_bytes, check,
+                   stream_status)
+    dev = torch.device("cuda")
+    M = max(pool[int(k)]["m"] for k in order)
+    N = max(pool[int(k)]["n"] for k in order)
+    i32, f32 = torch.int32, torch.float32
+    src, dst, so, do = (torch.empty(M, dtype=i32, device=dev) for _ in range(4))
+    col, val = torch.empty(M, dtype=i32, device=dev), torch.empty(M, dtype=f32, device=dev)
+    perm = torch.empty(N, dtype=i32, device=dev)
+    row_ptr = torch.empty(N + 1, dtype=torch.int64, device=dev)
+    x, y = torch.empty(N, dtype=f32, device=dev), torch.empty(N, dtype=f32, device=dev)
+    wr = torch.empty(max(boba_reorder_workspace_bytes(pool[int(k)]["m"], pool[int(k)]["n"])
+                         for k in order), dtype=torch.uint8, device=dev)
+    wc = torch.empty(max(boba_coo_to_csr_workspace_bytes(pool[int(k)]["m"], pool[int(k)]["n"])
+                         for k in order), dtype=torch.uint8, device=dev)
+    wsp = torch.empty(max(256, max(boba_spmv_workspace_bytes(pool[int(k)]["n"], pool[int(k)]["m"])
+                                   for k in order)), dtype=torch.uint8, device=dev)
+    ys = [_pinned_out(pool[int(k)]["n"]) for k in order]
+    perms = [torch.empty(pool[int(k)]["n"], dtype=i32, pin_memory=True) for k in order]
+    s = torch.cuda.current_stream()
+
+    def one(i, k):
+        g = pool[int(k)]
+        m, n = g["m"], g["n"]
+        src[:m].copy_(g["src"], non_blocking=True)
+        dst[:m].copy_(g["dst"], non_blocking=True)
+        x[:n].copy_(g["x"], non_blocking=True)
+        check(boba_reorder_ex(src[:m], dst[:m], m, n, perm[:n], so[:m], do[:m], None, wr,
+                              wr.numel(), s), "reorder")
+        check(boba_coo_to_csr(so[:m], do[:m], m, n, row_ptr[:n + 1], col[:m], val[:m], wc,
+                              wc.numel(), s), "csr")
+        for _ in range(spmv_iters):
+            check(boba_spmv_csr(row_ptr[:n + 1], col[:m], val[:m], x[:n], y[:n], n, m, wsp,
+                                wsp.numel(), s), "spmv")
+        ys[i].copy_(y[:n], non_blocking=True)
+        perms[i].copy_(perm[:n], non_blocking=True)
+
+    one(0, order[0])                                     # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, k in enumerate(order):
+        one(i, k)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    stream_status(s)
+    edges = sum(pool[int(k)]["m"] for k in order)
+    return {"wall_s": t1 - t0, "gedges_s_wall": edges / (t1 - t0) / 1e9,
+            "requests": len(order)}, ys, perms
+
+
+def serve_vs_sequential(n_requests: int = 48, pool_size: int = 24, seed: int = 0xB0BA0004,
+                        budget_bytes: int = 120 << 30, spmv_iters: int = 10,
+                        max_active: int = 64, m_lo: float = 1e4, m_hi: float = 1e8, pool=None):
+    """Saturated serving against the same request list run one request at a time
+    through the per-graph entry points; outputs compared bit for bit."""
+    pool = request_pool(pool_size, seed, m_lo, m_hi) if pool is None else pool
+    order = request_order(n_requests, len(pool), seed)
+    sat, ys_a, perms_a = run_saturated(pool, order, budget_bytes, spmv_iters, max_active)
+    seq, ys_b, perms_b = run_sequential(pool, order, spmv_iters)
+    identical = all(torch.equal(a, b) for a, b in zip(ys_a, ys_b)) and \
+        all(torch.equal(a, b) for a, b in zip(perms_a, perms_b))
+    return {"saturated": sat, "sequential": seq, "identical": bool(identical),
+            "speedup_served_vs_sequential": sat["gedges_s_wall"] / seq["gedges_s_wall"],
+            "n_requests": int(n_requests), "edges": int(sum(pool[int(k)]["m"] for k in order))}

@@ -47,6 +47,11 @@ def test_mix_equals_alone_and_oracle(serve):
         assert len(done) == 36 and all(st == 0 for _, _, st in done)
         st = srv.stats()
         assert st["requests"] == 36 and st["peak_pool_bytes"] <= 2 << 30
+        # continuous batching: requests joined while others were on the GPU, and
+        # the device work of several requests overlapped in time
+        assert st["peak_active"] > 1, st
+        assert st["joined_while_busy"] > 0, st
+        assert st["peak_device_overlap"] > 1, st
     for i, y, p in outs:
         assert torch.equal(y, alone[i][0]), i
         assert torch.equal(p, alone[i][1]), i
@@ -110,3 +115,14 @@ def test_poisson_stream_small(serve):
     st = serve.serve_workload(n_requests=60, pool_size=8, load=0.8, m_lo=1e4, m_hi=2e6,
                               budget_bytes=8 << 30, spmv_iters=10)
     assert st["requests"] == 60 and st["p99_ms"] >= st["p50_ms"] > 0 and st["gedges_s"] > 0
+
+
+def test_saturated_server_equals_one_request_at_a_time(serve):
+    """The served results at saturation equal, bit for bit, the same requests run
+    one after another through boba_reorder_ex / boba_coo_to_csr / boba_spmv_csr."""
+    res = serve.serve_vs_sequential(n_requests=20, pool_size=6, m_lo=1e4, m_hi=5e5,
+                                    budget_bytes=4 << 30, spmv_iters=3, max_active=16)
+    assert res["identical"]
+    sat = res["saturated"]
+    assert sat["requests"] == 20 and sat["peak_active"] > 1
+    assert res["sequential"]["requests"] == 20
