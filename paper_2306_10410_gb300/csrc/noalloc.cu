@@ -108,8 +108,10 @@ extern "C" boba_status_t boba_reorder_static(const int32_t *src, const int32_t *
     if (m > kStaticMaxM || n > kStaticMaxN) return BOBA_ERR_TOO_LARGE;
     if (n == 0 && m > 0) return BOBA_ERR_INVALID_ARG;
     if (n == 0) return BOBA_OK;
-    if (perm_out == nullptr || src_out == nullptr || dst_out == nullptr) return BOBA_ERR_INVALID_ARG;
-    if (m > 0 && (src == nullptr || dst == nullptr)) return BOBA_ERR_INVALID_ARG;
+    if (perm_out == nullptr) return BOBA_ERR_INVALID_ARG;
+    // with no edges there is nothing to read or rewrite: those four may be NULL
+    if (m > 0 && (src == nullptr || dst == nullptr || src_out == nullptr || dst_out == nullptr))
+        return BOBA_ERR_INVALID_ARG;
     ReorderLayout L;
     if (!reorder_layout(m, n, L) || L.total > kStaticScratchBytes) return BOBA_ERR_TOO_LARGE;
 

@@ -84,3 +84,39 @@ def test_static_entry_limits_and_errors():
     torch.cuda.synchronize()
     assert rc == 0 and int(err.item()) == 0
     assert perm.cpu().tolist() == [0, 1, 3, 2, 4]
+
+
+def test_static_entry_misaligned_views_and_no_edges():
+    """Inputs one element into their buffers (not 16-byte aligned: the scalar
+    first-occurrence and relabel kernels run), and a graph with no edges (only
+    the key initialisation and the rank kernel run); each bit for bit equal to
+    boba_reorder_ex, twice in a row."""
+    import paper_2306_10410_gb300 as boba
+    lib = boba.load()
+    stream = torch.cuda.current_stream()
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    I, J = synth.rmat(15, 300_001, seed=43, n=30_011)
+    srcb = torch.from_numpy(np.concatenate([[0], I]).astype(np.int32)).cuda()
+    dstb = torch.from_numpy(np.concatenate([[0], J]).astype(np.int32)).cuda()
+    src, dst = srcb[1:], dstb[1:]
+    assert src.data_ptr() % 16 != 0 and dst.data_ptr() % 16 != 0
+    for _ in range(2):
+        perm_ref, so_ref, do_ref = boba.reorder(src, dst, 30_011)
+        boba.stream_status()
+        rc, perm, so, do = _call_static(lib, src, dst, 30_011, err, stream)
+        assert rc == 0, boba.boba_status_string(rc)
+        torch.cuda.synchronize()
+        assert int(err.item()) == 0
+        assert torch.equal(perm, perm_ref)
+        assert torch.equal(so, so_ref)
+        assert torch.equal(do, do_ref)
+    empty = torch.zeros(0, dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        perm_ref, _, _ = boba.reorder(empty, empty, 7)
+        boba.stream_status()
+        rc, perm, so, do = _call_static(lib, empty, empty, 7, err, stream)
+        assert rc == 0, boba.boba_status_string(rc)
+        torch.cuda.synchronize()
+        assert int(err.item()) == 0
+        assert torch.equal(perm, perm_ref)
+        assert perm.cpu().tolist() == list(range(7))
