@@ -16,6 +16,17 @@ Printed (rank 0, one JSON line):
                its mean event-timed duration, against the measured HBM copy
                bandwidth
   cpu_baseline the CPU oracle (single-threaded C) on a bounded sample
+  spmv_error   relative L2 error of the timed fp32 SpMV against the fp64
+               oracle product, on the BOBA and the random order (the oracle
+               runs in spawned worker processes beside the GPU work, on the
+               synthetic input, never on anything the GPU produced)
+  perm_only    the permutation alone (no edge rewrite), the figure the
+               paper times
+  configs2     the low-skew workloads (4096^2 grid, Erdos-Renyi 2^24 / 2^27)
+  latency      the R-MAT scale-14 graph (L2-resident): one reorder's latency
+  gather_ceiling  random 4-byte loads per second from global, shared and
+               cluster-distributed shared memory, the ceiling of the two
+               lookup passes of the reorder
 
 ``--impl reference`` times the CPU oracle instead (the method has no other
 implementation to run), on the same workload, metric and unit.
@@ -154,6 +165,58 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# fp64 oracle products, computed in spawned worker processes
+# ---------------------------------------------------------------------------
+
+def oracle_y(workload_name, order):
+    """y = A x in fp64 by the oracle for a workload in `order` ("boba": the
+    oracle's own BOBA relabelling of the synthetic input; "random": the input
+    order), with the x the bench uses.  Runs in a worker process; only synth/
+    and oracle/ are used."""
+    import synth
+    import oracle
+    w = synth.WORKLOADS[workload_name]
+    I, J = w.generate()
+    if order == "boba":
+        _, I, J = oracle.reorder(I, J, w.n)
+    rp, col, val = oracle.coo_to_csr(I, J, w.n)
+    del I, J
+    x = synth.uniform_f32(w.n, seed=w.seed)
+    return oracle.spmv_f64(rp, col, val, x)
+
+
+def start_oracle_jobs(names, workers=4):
+    """Start the oracle products for `names` x (boba, random) in spawned
+    processes; call before the first CUDA call."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    ex = cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+    futs = {(nm, o): ex.submit(oracle_y, nm, o) for nm in names for o in ("boba", "random")}
+    return ex, futs
+
+
+def rel_l2(y32, y64):
+    y32 = np.asarray(y32, dtype=np.float64)
+    nrm = float(np.linalg.norm(y64))
+    return float(np.linalg.norm(y32 - y64) / nrm) if nrm > 0 else float(np.linalg.norm(y32))
+
+
+def spmv_errors(futs, name, ys, timeout=900):
+    """{order: rel-L2 of the GPU y against the oracle} for the orders in ys."""
+    out = {}
+    for order, y in ys.items():
+        f = futs.get((name, order)) if futs else None
+        if f is None or y is None:
+            out[order] = None
+            continue
+        try:
+            out[order] = round(rel_l2(y, f.result(timeout=timeout)), 10)
+        except Exception as exc:                     # report, do not hide
+            out[order] = "oracle failed: " + str(exc)[:120]
+    return out
+
+
+# ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
 
@@ -164,6 +227,16 @@ def run_ours(args):
     from paper_2306_10410_gb300 import build as bb
 
     world, rank, local = dist_env()
+    w = synth.WORKLOADS[args.workload]
+    # the oracle's fp64 products start before the first CUDA call (spawned
+    # processes) and run beside the GPU work
+    oracle_names = []
+    if args.spmv_error and rank == 0 and args.spmv_iters > 0:
+        oracle_names.append(w.name)
+        if args.configs2 and world == 1:
+            oracle_names += [synth.GRID4096.name, synth.ER24.name]
+    oracle_ex, oracle_futs = (start_oracle_jobs(oracle_names) if oracle_names
+                              else (None, {}))
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
@@ -171,7 +244,6 @@ def run_ours(args):
     bb.build()
     boba.load()
 
-    w = synth.WORKLOADS[args.workload]
     m, n = w.m, w.n
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
@@ -272,6 +344,22 @@ def run_ours(args):
         barrier()
     clocks = sampler.stop()
     boba.stream_status(stream)
+    # the last product of the last step: the timed SpMV on the BOBA order
+    y_boba = y.cpu().numpy() if have_csr and args.spmv_iters > 0 else None
+
+    # the permutation alone (src_out = dst_out = NULL): what the paper times
+    t_perm = []
+    for _ in range(max(3, min(args.steps, 5)) + 1):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        boba.check(boba.boba_reorder_ex(src, dst, m, n, perm, None, None, label, ws_r,
+                                        ws_r.numel(), stream), "reorder (perm only)")
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        t_perm.append(ev[0].elapsed_time(ev[1]))
+    boba.stream_status(stream)
+    perm_ms = statistics.median(t_perm[1:])
 
     t_reorder = [e[0].elapsed_time(e[1]) for e in evs]
     t_step = [e[0].elapsed_time(e[3]) for e in evs]
@@ -312,9 +400,11 @@ def run_ours(args):
                 "frac_nominal": round(kern[dom]["achieved_gbs"] / HBM_NOMINAL_GBS, 4)}
     # SpMV and CSR on the BOBA order vs the random (input) order, same kernels
     compare = None
+    y_random = None
     if have_csr:
         compare = compare_orders(args, boba, torch, dev, stream, src, dst, so, do, m, n,
                                  row_ptr, col, val, ws_c, ws_s, x, y, flush)
+        y_random = compare.pop("_y_random", None)
     if compare is not None:
         # the whole pipeline on each order (Sec. 5.6): what a user pays to go
         # from the edge list to spmv_iters products, and how many products it
@@ -328,9 +418,36 @@ def run_ours(args):
             "break_even_spmv_iters": (round((reorder_ms + o["csr_ms"] - r["csr_ms"]) / gain, 1)
                                       if gain > 0 else None)}
     full = 24 * m + 4 * n
+    reorder_traffic = reorder_dram_traffic(args.workload)
     reorder_roof = {"alg_bytes": full, "achieved_gbs": round(full / (reorder_ms * 1e-3) / 1e9, 1),
                     "frac": round(full / (reorder_ms * 1e-3) / 1e9 / hbm, 4),
-                    "frac_nominal": round(full / (reorder_ms * 1e-3) / 1e9 / HBM_NOMINAL_GBS, 4)}
+                    "frac_nominal": round(full / (reorder_ms * 1e-3) / 1e9 / HBM_NOMINAL_GBS, 4),
+                    "peak": hbm, "peak_source": peak_kind, "traffic": reorder_traffic}
+    perm_bytes = 8 * m + 4 * n
+    perm_only = {"ms": round(perm_ms, 4), "gedges_s": round(m / (perm_ms * 1e-3) / 1e9, 3),
+                 "alg_bytes": perm_bytes,
+                 "achieved_gbs": round(perm_bytes / (perm_ms * 1e-3) / 1e9, 1),
+                 "frac": round(perm_bytes / (perm_ms * 1e-3) / 1e9 / hbm, 4),
+                 "frac_nominal": round(perm_bytes / (perm_ms * 1e-3) / 1e9 / HBM_NOMINAL_GBS, 4)}
+    target = {"reorder_frac_of_hbm": 0.60, "reorder_frac": reorder_roof["frac"],
+              "met": bool(reorder_roof["frac"] >= 0.60),
+              "note": "the reorder looks up one entry of an n-sized array per endpoint twice "
+                      "(key, then label); see gather_ceiling for the rate those lookups allow"}
+
+    gather = None
+    if args.gather and world == 1:
+        gather = run_gather_probe(args, boba, torch, dev, stream, reorder_ms, m, kt.result)
+    latency = None
+    if args.latency and world == 1:
+        latency = run_latency(args, boba, torch, dev, stream)
+    configs2 = None
+    if args.configs2 and world == 1:
+        configs2 = run_configs2(args, boba, torch, dev, stream, flush, oracle_futs)
+    spmv_err = None
+    if oracle_futs:
+        spmv_err = spmv_errors(oracle_futs, w.name, {"boba": y_boba, "random": y_random})
+        spmv_err["bound"] = 1e-5
+        spmv_err["kernel"] = f"tuned SpMV variant {(tuning or {}).get('spmv', 0)} (the timed one)"
 
     # end-to-end through the public API with host buffers
     e2e = None if args.no_e2e else run_e2e(args, boba, torch, dev, stream, src_h, dst_h, m, n,
@@ -339,19 +456,38 @@ def run_ours(args):
     serving = None
     if args.serve and world == 1:
         from paper_2306_10410_gb300 import serve as sv
-        serving = sv.serve_workload(n_requests=args.serve_requests, pool_size=args.serve_pool,
-                                    load=0.8, budget_bytes=120 << 30, spmv_iters=10)
+        req_pool = sv.request_pool(args.serve_pool, 0xB0BA0004)
+        serving = sv.serve_workload(n_requests=args.serve_requests, load=0.8,
+                                    budget_bytes=120 << 30, spmv_iters=10, pool=req_pool)
         serving = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in serving.items()}
         serving["workload"] = ("Poisson stream of BOBA + CSR + 10x SpMV requests, R-MAT or grid, "
                                "m log-uniform in [1e4, 1e8], offered load 0.8, HBM budget 120 GB")
+        # saturation (every request submitted at once) against the same list run
+        # one request at a time through the per-graph entry points, same outputs
+        cmp_ = sv.serve_vs_sequential(n_requests=2 * args.serve_pool, budget_bytes=120 << 30,
+                                      spmv_iters=10, pool=req_pool)
+        del req_pool
+
+        def rnd(d):
+            return {k: (round(v, 4) if isinstance(v, float) else v) for k, v in d.items()}
+        serving["saturated"] = rnd(cmp_["saturated"])
+        serving["sequential"] = rnd(cmp_["sequential"])
+        serving["saturated_gedges_s"] = round(cmp_["saturated"]["gedges_s_wall"], 4)
+        serving["sequential_gedges_s"] = round(cmp_["sequential"]["gedges_s_wall"], 4)
+        serving["speedup_served_vs_sequential"] = round(cmp_["speedup_served_vs_sequential"], 3)
+        serving["identical"] = cmp_["identical"]
+        serving["saturated_requests"] = cmp_["n_requests"]
 
     batched = None
     if args.batched and world == 1:
         del src_h, dst_h
         batched = run_batched(args, boba, torch, dev, stream, flush, n_batch=args.batch_graphs)
 
+    if oracle_ex is not None:
+        oracle_ex.shutdown(wait=True, cancel_futures=True)
     result = {
-        "metric": METRIC, "value": round(value, 3), "unit": "Gedges/s", "n_gpus": world,
+        "metric": METRIC, "value": round(value, 3),
+        "value_hbm_frac": reorder_roof["frac"], "unit": "Gedges/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
@@ -363,6 +499,12 @@ def run_ours(args):
                       "csr": round(statistics.mean(t_csr), 4) if t_csr else None,
                       "spmv_total": round(statistics.mean(t_spmv), 4) if t_spmv else None},
         "reorder_roofline": reorder_roof,
+        "target": target,
+        "perm_only": perm_only,
+        "spmv_rel_l2_vs_fp64": spmv_err,
+        "gather_ceiling": gather,
+        "latency": latency,
+        "configs2": configs2,
         "tuning": tuning,
         "orders": compare,
         "roofline": roof,
@@ -405,6 +547,8 @@ def compare_orders(args, boba, torch, dev, stream, src, dst, so, do, m, n, row_p
                 t_csr.append(ev[0].elapsed_time(ev[1]))
                 t_spmv.append(ev[1].elapsed_time(ev[2]) / max(1, args.spmv_iters))
         boba.stream_status(stream)
+        if name == "random" and args.spmv_iters > 0:
+            out["_y_random"] = y.cpu().numpy()         # the timed kernel's product
         ms = statistics.median(t_spmv)
         out[name] = {"csr_ms": round(statistics.median(t_csr), 4), "spmv_ms": round(ms, 4),
                      "spmv_gbs": round(spmv_bytes / (ms * 1e-3) / 1e9, 1)}
@@ -589,6 +733,35 @@ def run_batched(args, boba, torch, dev, stream, flush, n_batch=4096, seed=None):
     boba.stream_status(stream)
     identical = bool(torch.equal(perm, perm1) and torch.equal(so, so1) and torch.equal(do, do1))
 
+    # every schedule of the batched call, each checked against the per-graph
+    # outputs: 0 is the one persistent launch (8-block clusters, keys in
+    # distributed shared memory), 1..5 the split schedules (a persistent launch
+    # for the small graphs, six grid-wide phase launches for the large ones)
+    sched = {}
+    names = {0: "cluster: plan + one persistent launch", 1: "split, sliced first <= 8, relabel <= 1",
+             2: "split, sliced first and relabel <= 8", 3: "split, sliced first <= 8, relabel <= 2",
+             4: "split, global phases", 5: "split, sliced first <= 3"}
+    for mode in range(6):
+        boba.boba_batched_set_mode(mode)
+        need = boba.boba_reorder_batched_workspace_bytes(n_batch, max_m, max_n, E, V)
+        if need > ws.numel():
+            ws = torch.empty(need, dtype=torch.uint8, device=dev)
+        perm.fill_(-1)
+        batched(stream)
+        boba.stream_status(stream)
+        same = bool(torch.equal(perm, perm1) and torch.equal(so, so1) and torch.equal(do, do1))
+        with boba.kernel_timing() as kt2:
+            batched(stream)
+            torch.cuda.synchronize(dev)
+        t = timed(batched, reps)
+        sched[mode] = {"form": names[mode], "ms": round(t, 3),
+                       "gedges_s": round(E / (t * 1e-3) / 1e9, 3),
+                       "launches": sum(c for _, c in kt2.result.values()),
+                       "bit_identical": same}
+        identical = identical and same
+    boba.boba_batched_set_mode(-1)
+    boba.stream_status(stream)
+
     # both forms captured once into a CUDA graph and replayed
     t_graph = {}
     for name, fn in (("batched", batched), ("per_graph", per_graph)):
@@ -618,6 +791,7 @@ def run_batched(args, boba, torch, dev, stream, flush, n_batch=4096, seed=None):
             "per_graph_gedges_s": round(E / (t_pergraph * 1e-3) / 1e9, 3),
             "speedup_batched_vs_per_graph": round(t_pergraph / t_batched, 3),
             "kernels_ms": split,
+            "schedules": sched,
             "cuda_graph_ms": t_graph,
             "schedule": {0: "split, sliced first <= 8 slices, relabel <= 1", 1: "cluster",
                          2: "split, sliced first and relabel <= 8 slices",
@@ -694,6 +868,219 @@ def run_e2e(args, boba, torch, dev, stream, src_h, dst_h, m, n, world):
             "api": "boba_reorder_host (chunked, copies overlapped with kernels); "
                    "steps alternate over 2 streams so step k+1's input copies overlap "
                    "step k's output copies"}
+
+
+def run_gather_probe(args, boba, torch, dev, stream, reorder_ms, m, kernel_times):
+    """Random 4-byte loads per second (boba_probe_gather) from a 64 MiB table in
+    global memory -- the size of the key and label arrays at n = 2^24 -- and
+    from smaller and larger tables, from one block's shared memory and from the
+    distributed shared memory of 8- and 16-block clusters; beside them the
+    lookups per second the reorder's two lookup passes reached."""
+    import ctypes
+    cases = [("global_64MiB", 0, 1 << 24, 0), ("global_4MiB", 0, 1 << 20, 0),
+             ("global_1GiB", 0, 1 << 28, 0), ("shared_128KiB", 1, 1 << 15, 0),
+             ("cluster8_1MiB", 2, 1 << 18, 8), ("cluster16_2MiB", 2, 1 << 19, 16)]
+    table = torch.randint(0, 1 << 30, (1 << 28,), dtype=torch.int32, device=dev)
+    out_words = 152 * 64 * 256
+    out = torch.empty(out_words, dtype=torch.int32, device=dev)
+    res = {}
+    for name, mode, words, cl in cases:
+        issued = ctypes.c_int64(0)
+        per_thread = 2048
+        times = []
+        rc = 0
+        for rep in range(4):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            rc = boba.boba_probe_gather(mode, table, words, per_thread, cl, out, out_words,
+                                        issued, stream)
+            ev[1].record(stream)
+            if rc != 0:
+                break
+            torch.cuda.synchronize(dev)
+            if rep:
+                times.append(ev[0].elapsed_time(ev[1]))
+        if rc != 0:
+            res[name] = {"unavailable": boba.boba_status_string(rc)}
+            continue
+        boba.stream_status(stream)
+        ms = statistics.median(times)
+        res[name] = {"loads_per_s": round(issued.value / (ms * 1e-3), 0), "ms": round(ms, 4),
+                     "loads": issued.value}
+    del table, out
+    # the reorder: 2m lookups in the first-occurrence pass, 2m in the relabel
+    look = {}
+    for k in ("reorder.first", "reorder.relabel"):
+        if k in kernel_times:
+            tot, launches = kernel_times[k]
+            look[k] = round(2 * m / (tot / max(1, launches) * 1e-3), 0)
+    g64 = res.get("global_64MiB", {}).get("loads_per_s")
+    return {"probe": res, "reorder_lookups_per_s": look,
+            "reorder_lookup_bound_ms": round(4 * m / g64 * 1e3, 4) if g64 else None,
+            "reorder_ms": round(reorder_ms, 4),
+            "note": "reorder_lookup_bound_ms = 4m lookups at the global_64MiB rate, with no "
+                    "stream traffic: the least time any one-lookup-per-endpoint design needs"}
+
+
+def run_latency(args, boba, torch, dev, stream):
+    """R-MAT scale 14 / 2^18 edges (fits in L2): the latency of one reorder,
+    eager and replayed from a CUDA graph, and of reorder + CSR + SpMV."""
+    import synth
+    w = synth.RMAT14
+    I, J = w.generate()
+    src, dst = torch.from_numpy(I).to(dev), torch.from_numpy(J).to(dev)
+    m, n = w.m, w.n
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    so, do = torch.empty_like(src), torch.empty_like(dst)
+    ws = torch.empty(boba.boba_reorder_workspace_bytes(m, n), dtype=torch.uint8, device=dev)
+    row_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(m, dtype=torch.int32, device=dev)
+    val = torch.empty(m, dtype=torch.float32, device=dev)
+    wc = torch.empty(boba.boba_coo_to_csr_workspace_bytes(m, n), dtype=torch.uint8, device=dev)
+    wsp = torch.empty(max(256, boba.boba_spmv_workspace_bytes(n, m)), dtype=torch.uint8,
+                      device=dev)
+    x = torch.from_numpy(synth.uniform_f32(n, seed=w.seed)).to(dev)
+    y = torch.empty(n, dtype=torch.float32, device=dev)
+
+    def reorder(st):
+        boba.check(boba.boba_reorder_ex(src, dst, m, n, perm, so, do, None, ws, ws.numel(), st),
+                   "reorder")
+
+    def pipeline(st):
+        reorder(st)
+        boba.check(boba.boba_coo_to_csr(so, do, m, n, row_ptr, col, val, wc, wc.numel(), st),
+                   "csr")
+        boba.check(boba.boba_spmv_csr(row_ptr, col, val, x, y, n, m, wsp, wsp.numel(), st),
+                   "spmv")
+
+    def lat(fn, reps=50):
+        for _ in range(3):
+            fn(stream)
+        torch.cuda.synchronize(dev)
+        out = []
+        for _ in range(reps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            fn(stream)
+            ev[1].record(stream)
+            ev[1].synchronize()
+            out.append(ev[0].elapsed_time(ev[1]))
+        return statistics.median(out)
+
+    res = {"workload": w.name, "m": m, "n": n,
+           "reorder_us": round(lat(reorder) * 1e3, 2),
+           "reorder_csr_spmv_us": round(lat(pipeline) * 1e3, 2)}
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            reorder(torch.cuda.current_stream(dev))
+        torch.cuda.synchronize(dev)
+        res["reorder_graph_replay_us"] = round(lat(lambda st: g.replay()) * 1e3, 2)
+        del g
+    except Exception as exc:
+        res["reorder_graph_replay_us"] = "capture failed: " + str(exc)[:120]
+    boba.stream_status(stream)
+    res["reorder_gedges_s"] = round(m / (res["reorder_us"] * 1e-6) / 1e9, 3)
+    res["note"] = "inputs stay in L2 (2 MiB); this is latency, not a roofline figure"
+    return res
+
+
+def run_configs2(args, boba, torch, dev, stream, flush, oracle_futs):
+    """The low-skew workloads: a 4096 x 4096 grid (both edge directions) and an
+    Erdos-Renyi graph with n = 2^24, m = 2^27, each relabelled at random with
+    edges shuffled: reorder (full and perm only), CSR and SpMV on the random and
+    the BOBA order, and the SpMV error against the fp64 oracle."""
+    import synth
+    hbm, _ = peaks()
+    res = {}
+    for w in (synth.GRID4096, synth.ER24):
+        m, n = w.m, w.n
+        I, J = w.generate()
+        src, dst = torch.from_numpy(I).to(dev), torch.from_numpy(J).to(dev)
+        del I, J
+        perm = torch.empty(n, dtype=torch.int32, device=dev)
+        so, do = torch.empty_like(src), torch.empty_like(dst)
+        ws = torch.empty(boba.boba_reorder_workspace_bytes(m, n), dtype=torch.uint8, device=dev)
+        row_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+        col = torch.empty(m, dtype=torch.int32, device=dev)
+        val = torch.empty(m, dtype=torch.float32, device=dev)
+        wc = torch.empty(boba.boba_coo_to_csr_workspace_bytes(m, n), dtype=torch.uint8,
+                         device=dev)
+        wsp = torch.empty(max(256, boba.boba_spmv_workspace_bytes(n, m)), dtype=torch.uint8,
+                          device=dev)
+        x = torch.from_numpy(synth.uniform_f32(n, seed=w.seed)).to(dev)
+        y = torch.empty(n, dtype=torch.float32, device=dev)
+        tuning = None
+        if args.tune:
+            tuning = boba.tune_reorder(src, dst, n, reps=3)
+            boba.check(boba.boba_reorder_ex(src, dst, m, n, perm, so, do, None, ws, ws.numel(),
+                                            stream), "reorder")
+            tuning.update(boba.tune_csr(so, do, n, reps=2))
+            boba.check(boba.boba_coo_to_csr(so, do, m, n, row_ptr, col, val, wc, wc.numel(),
+                                            stream), "csr")
+            tuning.update(boba.tune_spmv(row_ptr, col, val, x, reps=3))
+            boba.stream_status(stream)
+
+        def timed(fn, reps=5):
+            out = []
+            for rep in range(reps + 1):
+                flush.zero_()
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                ev[0].record(stream)
+                fn()
+                ev[1].record(stream)
+                torch.cuda.synchronize(dev)
+                if rep:
+                    out.append(ev[0].elapsed_time(ev[1]))
+            boba.stream_status(stream)
+            return statistics.median(out)
+
+        t_full = timed(lambda: boba.check(boba.boba_reorder_ex(
+            src, dst, m, n, perm, so, do, None, ws, ws.numel(), stream), "reorder"))
+        t_perm = timed(lambda: boba.check(boba.boba_reorder_ex(
+            src, dst, m, n, perm, None, None, None, ws, ws.numel(), stream), "reorder"))
+        boba.check(boba.boba_reorder_ex(src, dst, m, n, perm, so, do, None, ws, ws.numel(),
+                                        stream), "reorder")
+        r = {"m": m, "n": n, "tuning": tuning,
+             "reorder_ms": round(t_full, 4), "gedges_s": round(m / (t_full * 1e-3) / 1e9, 3),
+             "frac": round((24 * m + 4 * n) / (t_full * 1e-3) / 1e9 / hbm, 4),
+             "perm_only_ms": round(t_perm, 4),
+             "perm_only_gedges_s": round(m / (t_perm * 1e-3) / 1e9, 3),
+             "perm_only_frac": round((8 * m + 4 * n) / (t_perm * 1e-3) / 1e9 / hbm, 4)}
+        ys = {}
+        for order, (s_, d_) in (("random", (src, dst)), ("boba", (so, do))):
+            t_csr = timed(lambda: boba.check(boba.boba_coo_to_csr(
+                s_, d_, m, n, row_ptr, col, val, wc, wc.numel(), stream), "csr"), reps=3)
+            t_spmv = timed(lambda: boba.check(boba.boba_spmv_csr(
+                row_ptr, col, val, x, y, n, m, wsp, wsp.numel(), stream), "spmv"))
+            ys[order] = y.cpu().numpy()
+            nbr32, _ = boba.nbr(row_ptr, col, ids_per_line=32)
+            r[order] = {"csr_ms": round(t_csr, 4), "spmv_ms": round(t_spmv, 4),
+                        "spmv_gbs": round((8 * m + 16 * n) / (t_spmv * 1e-3) / 1e9, 1),
+                        "nbr32": round(nbr32, 5)}
+        r["spmv_speedup_boba_vs_random"] = round(r["random"]["spmv_ms"] / r["boba"]["spmv_ms"], 3)
+        r["spmv_rel_l2_vs_fp64"] = spmv_errors(oracle_futs, w.name, ys)
+        res[w.name] = r
+        del src, dst, perm, so, do, ws, row_ptr, col, val, wc, wsp, x, y
+        torch.cuda.empty_cache()
+    return res
+
+
+def reorder_dram_traffic(workload):
+    """DRAM bytes per reorder (sum over its kernels) from the committed ncu
+    summary, when every kernel of the reorder has a figure."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f).get(workload, {})
+    except Exception:
+        return None
+    parts = [d.get(k) for k in ("reorder.first", "reorder.relabel")]
+    if any(v is None for v in parts):
+        return None
+    return int(sum(parts) + sum(v for k, v in d.items()
+                                if k.startswith("reorder.") and k not in
+                                ("reorder.first", "reorder.relabel")))
 
 
 def load_traffic(kernel, workload):
@@ -786,8 +1173,27 @@ def main():
                     help="1: also run the serving workload (Poisson requests, HBM budget)")
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-pool", type=int, default=24)
+    ap.add_argument("--spmv-error", type=int, default=1,
+                    help="1: report the SpMV's rel-L2 error against the fp64 oracle")
+    ap.add_argument("--configs2", type=int, default=1,
+                    help="1: also run the grid 4096^2 and ER 2^24 / 2^27 workloads")
+    ap.add_argument("--latency", type=int, default=1,
+                    help="1: also time one reorder of R-MAT scale 14 (latency)")
+    ap.add_argument("--gather", type=int, default=1,
+                    help="1: also measure the random-load ceiling (boba_probe_gather)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)        # at least 3 untimed warm-up steps
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # one process per GPU: relaunch this command under torch.distributed.run
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+               f"--nproc-per-node={args.gpus}", "--master-addr", "127.0.0.1",
+               "--master-port", os.environ.get("MASTER_PORT", "29533"),
+               os.path.abspath(__file__)] + sys.argv[1:]
+        sys.exit(subprocess.call(cmd))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world != args.gpus:
+        print(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={world}; using {world}",
+              file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
     else:
