@@ -418,7 +418,7 @@ def run_ours(args):
             "break_even_spmv_iters": (round((reorder_ms + o["csr_ms"] - r["csr_ms"]) / gain, 1)
                                       if gain > 0 else None)}
     full = 24 * m + 4 * n
-    reorder_traffic = reorder_dram_traffic(args.workload)
+    reorder_traffic = reorder_dram_traffic(args.workload, m, n)
     reorder_roof = {"alg_bytes": full, "achieved_gbs": round(full / (reorder_ms * 1e-3) / 1e9, 1),
                     "frac": round(full / (reorder_ms * 1e-3) / 1e9 / hbm, 4),
                     "frac_nominal": round(full / (reorder_ms * 1e-3) / 1e9 / HBM_NOMINAL_GBS, 4),
@@ -434,6 +434,10 @@ def run_ours(args):
               "note": "the reorder looks up one entry of an n-sized array per endpoint twice "
                       "(key, then label); see gather_ceiling for the rate those lookups allow"}
 
+    variants = None
+    if args.tune and not args.tune_spec and world == 1:
+        variants = time_reorder_variants(boba, torch, dev, stream, flush, src, dst, m, n, perm,
+                                         so, do, ws_r, tuning)
     gather = None
     if args.gather and world == 1:
         gather = run_gather_probe(args, boba, torch, dev, stream, reorder_ms, m, kt.result)
@@ -503,6 +507,8 @@ def run_ours(args):
         "perm_only": perm_only,
         "spmv_rel_l2_vs_fp64": spmv_err,
         "gather_ceiling": gather,
+        "lookup_roofline": lookup_roofline(gather),
+        "reorder_variants_ms": variants,
         "latency": latency,
         "configs2": configs2,
         "tuning": tuning,
@@ -878,6 +884,7 @@ def run_gather_probe(args, boba, torch, dev, stream, reorder_ms, m, kernel_times
     lookups per second the reorder's two lookup passes reached."""
     import ctypes
     cases = [("global_64MiB", 0, 1 << 24, 0), ("global_4MiB", 0, 1 << 20, 0),
+             ("global_128KiB", 0, 1 << 15, 0),
              ("global_1GiB", 0, 1 << 28, 0), ("shared_128KiB", 1, 1 << 15, 0),
              ("cluster8_1MiB", 2, 1 << 18, 8), ("cluster16_2MiB", 2, 1 << 19, 16)]
     table = torch.randint(0, 1 << 30, (1 << 28,), dtype=torch.int32, device=dev)
@@ -914,12 +921,59 @@ def run_gather_probe(args, boba, torch, dev, stream, reorder_ms, m, kernel_times
         if k in kernel_times:
             tot, launches = kernel_times[k]
             look[k] = round(2 * m / (tot / max(1, launches) * 1e-3), 0)
+    if "spmv" in kernel_times:
+        tot, launches = kernel_times["spmv"]
+        look["spmv"] = round(m / (tot / max(1, launches) * 1e-3), 0)
     g64 = res.get("global_64MiB", {}).get("loads_per_s")
-    return {"probe": res, "reorder_lookups_per_s": look,
+    if g64:
+        look_frac = {k: round(v / g64, 4) for k, v in look.items()}
+    else:
+        look_frac = None
+    return {"probe": res, "reorder_lookups_per_s": look, "lookups_frac_of_ceiling": look_frac,
             "reorder_lookup_bound_ms": round(4 * m / g64 * 1e3, 4) if g64 else None,
             "reorder_ms": round(reorder_ms, 4),
             "note": "reorder_lookup_bound_ms = 4m lookups at the global_64MiB rate, with no "
                     "stream traffic: the least time any one-lookup-per-endpoint design needs"}
+
+
+def lookup_roofline(gather):
+    """The lookup passes against the measured random-load ceiling: random loads
+    per second each reached over the probe's rate from a 64 MiB table."""
+    if not gather or not gather.get("lookups_frac_of_ceiling"):
+        return None
+    peak = gather["probe"]["global_64MiB"]["loads_per_s"]
+    return {"bound": "random 4-byte loads (L1TEX/L2 request rate)", "unit": "loads/s",
+            "peak": peak, "peak_source": "boba_probe_gather, 64 MiB table, measured in this run",
+            "achieved": gather["reorder_lookups_per_s"],
+            "frac": gather["lookups_frac_of_ceiling"]}
+
+
+def time_reorder_variants(boba, torch, dev, stream, flush, src, dst, m, n, perm, so, do, ws,
+                          tuning, reps=5):
+    """Device time of the first-occurrence and relabel kernels for every variant
+    (0..5 launch shapes, 6 warp-aggregated), the other family
+    at its tuned choice; restores the tuned choices."""
+    out = {}
+    for fam_name, fam, key in (("first", boba.TUNE_FIRST, "reorder.first"),
+                               ("relabel", boba.TUNE_RELABEL, "reorder.relabel")):
+        res = {}
+        for v in range(7):
+            boba.load().boba_tune_set(fam, m, v)
+            boba.check(boba.boba_reorder_ex(src, dst, m, n, perm, so, do, None, ws, ws.numel(),
+                                            stream), "reorder")
+            tot = 0.0
+            for _ in range(reps):
+                flush.zero_()
+                with boba.kernel_timing() as kt:
+                    boba.check(boba.boba_reorder_ex(src, dst, m, n, perm, so, do, None, ws,
+                                                    ws.numel(), stream), "reorder")
+                    torch.cuda.synchronize(dev)
+                tot += kt.result[key][0]
+            res[v] = round(tot / reps, 4)
+        boba.load().boba_tune_set(fam, m, (tuning or {}).get(fam_name, 0))
+        out[fam_name] = res
+    boba.stream_status(stream)
+    return out
 
 
 def run_latency(args, boba, torch, dev, stream):
@@ -1066,21 +1120,23 @@ def run_configs2(args, boba, torch, dev, stream, flush, oracle_futs):
     return res
 
 
-def reorder_dram_traffic(workload):
-    """DRAM bytes per reorder (sum over its kernels) from the committed ncu
-    summary, when every kernel of the reorder has a figure."""
+def reorder_dram_traffic(workload, m=None, n=None):
+    """DRAM bytes per launch of the reorder's two lookup kernels from the
+    committed ncu summary, beside their algorithmic bytes."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             d = json.load(f).get(workload, {})
     except Exception:
         return None
-    parts = [d.get(k) for k in ("reorder.first", "reorder.relabel")]
-    if any(v is None for v in parts):
-        return None
-    return int(sum(parts) + sum(v for k, v in d.items()
-                                if k.startswith("reorder.") and k not in
-                                ("reorder.first", "reorder.relabel")))
+    out = {}
+    alg = algorithmic_bytes(m, n, m) if m else {}
+    for k in ("reorder.first", "reorder.relabel"):
+        if d.get(k) is None:
+            continue
+        out[k] = {"dram_bytes": d[k], "alg_bytes": alg.get(k),
+                  "ratio": round(d[k] / alg[k], 3) if alg.get(k) else None}
+    return out or None
 
 
 def load_traffic(kernel, workload):

@@ -15,9 +15,7 @@
 // iff position i of I ++ J is the first occurrence of its vertex, which is the
 // flag key[I[i]] == i of the method, built from the n keys instead of a second
 // pass over the 2m positions.
-#include <algorithm>
 #include <cstdio>
-#include <mutex>
 
 #include "common.cuh"
 #include "host.hpp"
@@ -479,121 +477,8 @@ void launch_relabel_v(const ReorderArgs &a, cudaStream_t stream)
                                                                   a.src_out, a.dst_out, a.status));
 }
 
-// ---------------------------------------------------------------------------
-// L2 residency of the looked-up array (variant 7 of both lookup kernels): the
-// launch carries an access-policy window over the key (or label) array with
-// hits marked persisting and the rest streaming, so the n-sized array keeps
-// its L2 lines against the edge streams.  The lines are set back to normal by
-// the next kernel that reads the whole array (k_mark for the keys, k_touch for
-// the labels) under a window marked normal, so later work (the CSR build)
-// gets the whole L2 back.  The process's persisting-L2 limit is raised to the
-// device maximum once per device when this variant first runs.
-// ---------------------------------------------------------------------------
-struct L2Window {
-    bool ok = false;
-    size_t max_window = 0, limit = 0;
-};
-
-const L2Window &l2_window_info()
-{
-    static std::mutex mu;
-    static L2Window info[64];
-    static bool done[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    dev &= 63;
-    std::lock_guard<std::mutex> lk(mu);
-    if (!done[dev]) {
-        done[dev] = true;
-        int maxw = 0, maxp = 0;
-        if (cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev) == cudaSuccess &&
-            maxw > 0 && maxp > 0 &&
-            cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)maxp) == cudaSuccess) {
-            info[dev].ok = true;
-            info[dev].max_window = (size_t)maxw;
-            info[dev].limit = (size_t)maxp;
-        } else {
-            (void)cudaGetLastError();
-        }
-    }
-    return info[dev];
-}
-
-// Launch `kern` with an access-policy window over [base, base + bytes).
-template <typename... KArgs, typename... Args>
-cudaError_t launch_windowed(void (*kern)(KArgs...), int grid, int block, cudaStream_t stream,
-                            const void *base, size_t bytes, cudaAccessProperty hit,
-                            Args... args)
-{
-    const L2Window &w = l2_window_info();
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((unsigned)block);
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    if (w.ok && bytes > 0) {
-        const size_t nb = bytes < w.max_window ? bytes : w.max_window;
-        attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
-        attr[0].val.accessPolicyWindow.base_ptr = const_cast<void *>(base);
-        attr[0].val.accessPolicyWindow.num_bytes = nb;
-        attr[0].val.accessPolicyWindow.hitRatio =
-            hit == cudaAccessPropertyPersisting ? (float)std::min(1.0, (double)w.limit / (double)nb)
-                                                : 1.0f;
-        attr[0].val.accessPolicyWindow.hitProp = hit;
-        attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-    }
-    return cudaLaunchKernelEx(&cfg, kern, args...);
-}
-
-// Reads every label once under a window marked normal (see above).
-__global__ void __launch_bounds__(256) k_touch(const int32_t *__restrict__ a, int64_t n,
-                                               uint32_t *sink)
-{
-    uint32_t acc = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        acc ^= (uint32_t)a[i];
-    if (acc == 0x9E3779B9u) atomicAdd(sink, 1u);      // keeps the loads; almost never taken
-}
-
-void launch_first_windowed(const ReorderArgs &a, cudaStream_t stream)
-{
-    constexpr int B = 256, U = 4;
-    const int64_t work = cdiv(2 * a.m, 4LL * B * U);
-    const int g = persistent_grid((const void *)k_first_v<B, U>, B, work);
-    cudaError_t e = cudaSuccess;
-    BOBA_TIMED("reorder.first", stream,
-               e = launch_windowed(k_first_v<B, U, false>, g, B, stream, a.key, (size_t)a.n * 4,
-                                   cudaAccessPropertyPersisting, a.src, a.dst, a.m, a.n, a.key,
-                                   a.status));
-    (void)e;
-}
-
-void launch_relabel_windowed(const ReorderArgs &a, cudaStream_t stream)
-{
-    constexpr int B = 256, U = 4;
-    const int64_t work = cdiv(2 * a.m, 4LL * B * U);
-    const int g = persistent_grid((const void *)k_relabel_v<B, U>, B, work);
-    cudaError_t e = cudaSuccess;
-    BOBA_TIMED("reorder.relabel", stream,
-               e = launch_windowed(k_relabel_v<B, U, false>, g, B, stream, a.label,
-                                   (size_t)a.n * 4, cudaAccessPropertyPersisting, a.src, a.dst,
-                                   a.m, a.n, (const int32_t *)a.label, a.src_out, a.dst_out,
-                                   a.status));
-    const int gt = persistent_grid((const void *)k_touch, 256, cdiv(a.n, 256));
-    BOBA_TIMED("reorder.relabel.reset", stream,
-               e = launch_windowed(k_touch, gt, 256, stream, a.label, (size_t)a.n * 4,
-                                   cudaAccessPropertyNormal, (const int32_t *)a.label,
-                                   (int64_t)a.n, a.counters + kCtrScratch));
-    (void)e;
-}
-
 // Variant table: index -> (block, loads in flight); 6 is the warp-aggregated
-// form of the default shape, 7 the default shape with the looked-up array
-// held persisting in L2.  Index 0 is the default.
+// form of the default shape.  Index 0 is the default.
 bool launch_first_variant(int v, const ReorderArgs &a, cudaStream_t s)
 {
     switch (v) {
@@ -603,7 +488,6 @@ bool launch_first_variant(int v, const ReorderArgs &a, cudaStream_t s)
     case 4: launch_first_v<128, 8>(a, s); return true;
     case 5: launch_first_v<512, 2>(a, s); return true;
     case 6: launch_first_v<256, 4, true>(a, s); return true;
-    case 7: launch_first_windowed(a, s); return true;
     default: return false;
     }
 }
@@ -617,7 +501,6 @@ bool launch_relabel_variant(int v, const ReorderArgs &a, cudaStream_t s)
     case 4: launch_relabel_v<128, 8>(a, s); return true;
     case 5: launch_relabel_v<512, 2>(a, s); return true;
     case 6: launch_relabel_v<256, 4, true>(a, s); return true;
-    case 7: launch_relabel_windowed(a, s); return true;
     default: return false;
     }
 }
@@ -639,7 +522,6 @@ template __global__ void k_relabel<false>(const int32_t *, const int32_t *, int6
 boba_status_t launch_reorder(const ReorderArgs &a, int64_t n4, size_t nzero_u32,
                              cudaStream_t stream)
 {
-    bool first_windowed = false;
     {
         const int64_t work = cdiv((int64_t)((size_t)n4 > nzero_u32 ? (size_t)n4 : nzero_u32) / 4, 256);
         const int g = persistent_grid((const void *)k_init, 256, work);
@@ -667,7 +549,6 @@ boba_status_t launch_reorder(const ReorderArgs &a, int64_t n4, size_t nzero_u32,
     } else if (a.m > 0) {
         const bool vec = aligned16(a.src) && aligned16(a.dst);
         const int64_t work = cdiv(2 * a.m, 4 * kFirstBlock * kFirstUnroll);
-        first_windowed = vec && tuned_variant(kTuneFirst, a.m) == 7;
         if (vec && launch_first_variant(tuned_variant(kTuneFirst, a.m), a, stream)) {
             // tuned variant launched
         } else if (vec) {
@@ -684,18 +565,7 @@ boba_status_t launch_reorder(const ReorderArgs &a, int64_t n4, size_t nzero_u32,
     }
     if (a.m > 0) {
         const int gm = persistent_grid((const void *)k_mark, 256, cdiv(n4 / 4, 256));
-        if (first_windowed) {
-            // k_mark reads every key: under a normal window it returns the
-            // persisting key lines to normal
-            cudaError_t e = cudaSuccess;
-            BOBA_TIMED("reorder.mark", stream,
-                       e = launch_windowed(k_mark, gm, 256, stream, a.key, (size_t)a.n * 4,
-                                           cudaAccessPropertyNormal, (const uint32_t *)a.key, n4,
-                                           a.bitmap));
-            BOBA_CUDA_TRY(e);
-        } else {
-            BOBA_TIMED("reorder.mark", stream, k_mark<<<gm, 256, 0, stream>>>(a.key, n4, a.bitmap));
-        }
+        BOBA_TIMED("reorder.mark", stream, k_mark<<<gm, 256, 0, stream>>>(a.key, n4, a.bitmap));
         BOBA_TIMED("reorder.scan", stream,
                    k_scan<<<(unsigned)a.scan_tiles, kScanBlock, 0, stream>>>(
                        a.bitmap, a.grp, a.tstat_scan, a.counters, a.scan_tiles, a.status));

@@ -19,7 +19,6 @@ constexpr int kEmitGroups = 4;                      // int4 groups of keys per t
 constexpr int kEmitTileVerts = kEmitBlock * 4 * kEmitGroups;   // 16 vertices per thread
 constexpr int kNumCounters = 8;                    // tickets and totals in the workspace
 constexpr int kCtrScanTicket = 0, kCtrEmitTicket = 1, kCtrTotal = 2;
-constexpr int kCtrScratch = 3;                     // a word kernels may write freely
 
 struct ReorderArgs {
     const int32_t *src, *dst;
