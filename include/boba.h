@@ -526,7 +526,9 @@ enum { BOBA_TUNE_FIRST = 0, BOBA_TUNE_RELABEL = 1, BOBA_TUNE_BATCHED = 2, BOBA_T
  * boba_tune_reorder -- times every variant of the first-occurrence kernel,
  * then of the relabel kernel (0..5: block size x loads in flight; 6: lanes of
  * a warp holding the same ID look it up once (warp-aggregated AtomicMin, and
- * one label gather shuffled to the group)), on this graph with
+ * one label gather shuffled to the group); 7: the edge streams moved between
+ * global and shared memory by bulk asynchronous copies, so that only the
+ * lookups go through L1), on this graph with
  * boba_reorder_ex's arguments, discards any variant whose perm/src_out/dst_out
  * differ from the default's in a single bit, and keeps the fastest for graphs
  * in the same power-of-two size class of m on this device.  chosen (int[2],

@@ -478,7 +478,8 @@ void launch_relabel_v(const ReorderArgs &a, cudaStream_t stream)
 }
 
 // Variant table: index -> (block, loads in flight); 6 is the warp-aggregated
-// form of the default shape.  Index 0 is the default.
+// form of the default shape, 7 the form whose edge streams move by bulk
+// asynchronous copies (reorder_tma.cu).  Index 0 is the default.
 bool launch_first_variant(int v, const ReorderArgs &a, cudaStream_t s)
 {
     switch (v) {
@@ -488,6 +489,7 @@ bool launch_first_variant(int v, const ReorderArgs &a, cudaStream_t s)
     case 4: launch_first_v<128, 8>(a, s); return true;
     case 5: launch_first_v<512, 2>(a, s); return true;
     case 6: launch_first_v<256, 4, true>(a, s); return true;
+    case 7: launch_first_tma(a, s); return true;
     default: return false;
     }
 }
@@ -501,6 +503,7 @@ bool launch_relabel_variant(int v, const ReorderArgs &a, cudaStream_t s)
     case 4: launch_relabel_v<128, 8>(a, s); return true;
     case 5: launch_relabel_v<512, 2>(a, s); return true;
     case 6: launch_relabel_v<256, 4, true>(a, s); return true;
+    case 7: launch_relabel_tma(a, s); return true;
     default: return false;
     }
 }

@@ -111,6 +111,11 @@ inline bool reorder_layout(int64_t m, int64_t n, ReorderLayout &L)
 boba_status_t launch_reorder(const ReorderArgs &a, int64_t n4, size_t nzero_u32,
                              cudaStream_t stream);
 
+// The lookup passes with their edge streams moved by bulk asynchronous copies
+// (reorder_tma.cu); vector path only (16-byte-aligned arrays).
+void launch_first_tma(const ReorderArgs &a, cudaStream_t stream);
+void launch_relabel_tma(const ReorderArgs &a, cudaStream_t stream);
+
 // The kernels of the pipeline (defined in reorder.cu).
 __global__ void k_init(uint32_t *__restrict__ key, int64_t n4, uint32_t *__restrict__ zero,
                        int64_t nzero);

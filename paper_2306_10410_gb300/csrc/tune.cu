@@ -1,6 +1,6 @@
 // Autotuner: for each kernel family with several correct launch variants
 // (block size and loads in flight of the first-occurrence and relabel
-// streams, their warp-aggregated form, the schedule of the
+// streams, their warp-aggregated and bulk-copy forms, the schedule of the
 // batched path, the SpMV kernel and shape --
 // lanes per row, or merge-path block, items and shared-memory carve-out --
 // and the ranking, tile shape and offset scheme (look-back or
@@ -32,7 +32,7 @@ constexpr int kClasses = 64;
 // variant must also stay within that of the default variant's fp32 result.
 constexpr double kSpmvTuneRelL2 = 1e-5;
 constexpr int kMaxDev = 64;
-constexpr int kVariants[kTuneKernels] = {7, 7, 6, 14, 10};   // first, relabel, batched, spmv, csr
+constexpr int kVariants[kTuneKernels] = {8, 8, 6, 14, 10};   // first, relabel, batched, spmv, csr
 const char *kNames[kTuneKernels] = {"first", "relabel", "batched", "spmv", "csr"};
 
 std::mutex g_tmu;

@@ -23,9 +23,9 @@ def test_every_reorder_variant_is_bit_exact(boba):
     n = 1 << 16
     operm, oso, odo = oracle.reorder(I, J, n)
     src, dst = torch.from_numpy(I).cuda(), torch.from_numpy(J).cuda()
-    # 0..5 launch shapes, 6 warp-aggregated lookups
+    # 0..5 launch shapes, 6 warp-aggregated lookups, 7 bulk-copied streams
     for kernel in (boba.TUNE_FIRST, boba.TUNE_RELABEL):
-        for v in range(7):
+        for v in range(8):
             boba.tune_reset()
             boba.load().boba_tune_set(kernel, len(I), v)
             assert boba.load().boba_tune_get(kernel, len(I)) == v
@@ -43,7 +43,7 @@ def test_tuner_picks_and_persists(boba, tmp_path):
     src, dst = torch.from_numpy(I).cuda(), torch.from_numpy(J).cuda()
     boba.tune_reset()
     ch = boba.tune_reorder(src, dst, n, reps=2)
-    assert 0 <= ch["first"] < 7 and 0 <= ch["relabel"] < 7
+    assert 0 <= ch["first"] < 8 and 0 <= ch["relabel"] < 8
     path = tmp_path / "tune.txt"
     boba.tune_save(path)
     boba.tune_reset()
