@@ -175,14 +175,45 @@ def test_idempotent_on_gpu(boba):
     np.testing.assert_array_equal(do2, do)
 
 
+N_LOOKUP_VARIANTS = 8      # first-occurrence and relabel launch variants of the tuner
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("wname", ["rmat24_m2^28", "grid4096", "er24_m2^27"])
 def test_full_size_bit_exact(boba, wname):
-    """The full-size workloads, in the launch configuration the benchmark times,
-    checked element by element against the oracle."""
+    """The full-size workloads checked element by element against the oracle:
+    the default launch configuration, then every first-occurrence and every
+    relabel variant the tuner may pick (the benchmark times the tuned ones),
+    each compared on the device with the oracle's arrays."""
     w = synth.WORKLOADS[wname]
     I, J = w.generate()
-    assert_parity(boba, I, J, w.n)
+    operm, olab = oracle.boba_perm(I, J, w.n)
+    oso, odo = oracle.relabel(I, J, olab, w.n)
+    src = torch.from_numpy(I).cuda()
+    dst = torch.from_numpy(J).cuda()
+    del I, J
+    ref = [torch.from_numpy(a).cuda() for a in (operm, olab, oso, odo)]
+    del operm, olab, oso, odo
+    perm = torch.empty(w.n, dtype=torch.int32, device="cuda")
+    lab = torch.empty(w.n, dtype=torch.int32, device="cuda")
+    so, do = torch.empty_like(src), torch.empty_like(dst)
+    lib = boba.load()
+    cases = [(None, 0)] + [(boba.TUNE_FIRST, v) for v in range(1, N_LOOKUP_VARIANTS)] + \
+            [(boba.TUNE_RELABEL, v) for v in range(1, N_LOOKUP_VARIANTS)]
+    try:
+        for fam, v in cases:
+            boba.tune_reset()
+            if fam is not None:
+                lib.boba_tune_set(fam, w.m, v)
+            for t in (perm, lab, so, do):
+                t.fill_(-7)
+            boba.reorder(src, dst, w.n, perm_out=perm, src_out=so, dst_out=do, label_out=lab)
+            boba.stream_status()
+            for name, got, want in zip(("perm", "label", "src_out", "dst_out"),
+                                       (perm, lab, so, do), ref):
+                assert torch.equal(got, want), (wname, fam, v, name)
+    finally:
+        boba.tune_reset()
 
 
 @pytest.mark.parametrize("shards", [1, 2, 3, 5])
