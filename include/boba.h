@@ -541,9 +541,10 @@ boba_status_t boba_tune_reorder(const int32_t *src, const int32_t *dst, int64_t 
 
 /*
  * boba_tune_batched -- the same for the schedule of boba_reorder_batched
- * (variant 0: split mode, 1: cluster mode), keyed by total_m.  A variant
- * that needs more scratch than ws_bytes is skipped.  An explicit
- * boba_batched_set_mode overrides the tuned choice.
+ * (variant 0: the default split schedule, boba_batched_set_mode 1; 1: the
+ * cluster mode, set_mode 0; 2 .. 5: the split schedules of set_mode 2 .. 5),
+ * keyed by total_m.  A variant that needs more scratch than ws_bytes is
+ * skipped.  An explicit boba_batched_set_mode overrides the tuned choice.
  */
 boba_status_t boba_tune_batched(const int32_t *src, const int32_t *dst, const int64_t *edge_off,
                                 const int64_t *vert_off, int64_t G, int64_t max_m, int64_t max_n,
