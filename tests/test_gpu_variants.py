@@ -69,3 +69,26 @@ def test_racy_store_is_valid_and_close(boba):
     v_exact, _ = boba.nbr(*[torch.from_numpy(a).cuda() for a in oracle.coo_to_csr(oso, odo, n)[:2]])
     v_racy, _ = boba.nbr(*[torch.from_numpy(a).cuda() for a in oracle.coo_to_csr(s, d, n)[:2]])
     assert abs(v_racy - v_exact) < 0.05
+
+
+@pytest.mark.slow
+def test_full_size_rmat24_variants(boba):
+    """R-MAT 24 / 2^28 edges, as the benchmark runs them: the interleaved
+    flattening bit-exact against the oracle, and the racy store a valid
+    permutation with consistent edges (checked on the device)."""
+    w = synth.RMAT24
+    I, J = w.generate()
+    src, dst = dev(I), dev(J)
+    perm, so, do = boba.reorder_variant(src, dst, w.n, 1)
+    boba.stream_status()
+    operm, olab = oracle.boba_perm_interleaved(I, J, w.n)
+    assert torch.equal(perm, dev(operm))
+    del operm
+    oso, odo = oracle.relabel(I, J, olab, w.n)
+    assert torch.equal(so, dev(oso)) and torch.equal(do, dev(odo))
+    del oso, odo, olab, perm, so, do
+    perm, so, do = boba.reorder_variant(src, dst, w.n, 2)
+    boba.stream_status()
+    p = perm.long()
+    assert torch.equal(torch.sort(p).values, torch.arange(w.n, device="cuda"))   # a permutation
+    assert torch.equal(perm[so.long()], src) and torch.equal(perm[do.long()], dst)
