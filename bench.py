@@ -447,6 +447,11 @@ def run_ours(args):
     configs2 = None
     if args.configs2 and world == 1:
         configs2 = run_configs2(args, boba, torch, dev, stream, flush, oracle_futs)
+    # the unit that binds the dominant kernel, measured: its random loads
+    # against the probe's ceiling (see gather_ceiling / lookup_roofline)
+    if roof is not None and gather and (gather.get("lookups_frac_of_ceiling") or {}).get(dom):
+        roof["limiter"] = {"unit": "L1TEX-to-crossbar request port (random loads that miss L1)",
+                           "frac_of_measured_ceiling": gather["lookups_frac_of_ceiling"][dom]}
     spmv_err = None
     if oracle_futs:
         spmv_err = spmv_errors(oracle_futs, w.name, {"boba": y_boba, "random": y_random})
