@@ -18,8 +18,8 @@ Printed (rank 0, one JSON line):
   cpu_baseline the CPU oracle (single-threaded C) on a bounded sample
   spmv_error   relative L2 error of the timed fp32 SpMV against the fp64
                oracle product, on the BOBA and the random order (the oracle
-               runs in spawned worker processes beside the GPU work, on the
-               synthetic input, never on anything the GPU produced)
+               runs in spawned worker processes beside the GPU-only legs, on
+               the synthetic input, never on anything the GPU produced)
   perm_only    the permutation alone (no edge rewrite), the figure the
                paper times
   configs2     the low-skew workloads (4096^2 grid, Erdos-Renyi 2^24 / 2^27)
@@ -187,7 +187,7 @@ def oracle_y(workload_name, order):
 
 def start_oracle_jobs(names, workers=4):
     """Start the oracle products for `names` x (boba, random) in spawned
-    processes; call before the first CUDA call."""
+    processes (spawned, not forked, so starting them after CUDA use is safe)."""
     import concurrent.futures as cf
     import multiprocessing as mp
     ex = cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
@@ -228,15 +228,15 @@ def run_ours(args):
 
     world, rank, local = dist_env()
     w = synth.WORKLOADS[args.workload]
-    # the oracle's fp64 products start before the first CUDA call (spawned
-    # processes) and run beside the GPU work
+    # the oracle's fp64 products run in spawned worker processes beside the
+    # GPU-only legs; they start after the host-buffer (e2e) leg, whose copies
+    # they would slow down through the host's memory
     oracle_names = []
     if args.spmv_error and rank == 0 and args.spmv_iters > 0:
         oracle_names.append(w.name)
         if args.configs2 and world == 1:
             oracle_names += [synth.GRID4096.name, synth.ER24.name]
-    oracle_ex, oracle_futs = (start_oracle_jobs(oracle_names) if oracle_names
-                              else (None, {}))
+    oracle_ex, oracle_futs = None, {}
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
@@ -398,6 +398,12 @@ def run_ours(args):
                 "peak": hbm, "unit": "GB/s", "frac": kern[dom]["frac"], "traffic": traffic,
                 "peak_source": peak_kind, "peak_nominal": HBM_NOMINAL_GBS,
                 "frac_nominal": round(kern[dom]["achieved_gbs"] / HBM_NOMINAL_GBS, 4)}
+    # end-to-end through the public API with host buffers
+    e2e = None if args.no_e2e else run_e2e(args, boba, torch, dev, stream, src_h, dst_h, m, n,
+                                           world)
+    if oracle_names:
+        oracle_ex, oracle_futs = start_oracle_jobs(oracle_names)
+
     # SpMV and CSR on the BOBA order vs the random (input) order, same kernels
     compare = None
     y_random = None
@@ -458,9 +464,9 @@ def run_ours(args):
         spmv_err["bound"] = 1e-5
         spmv_err["kernel"] = f"tuned SpMV variant {(tuning or {}).get('spmv', 0)} (the timed one)"
 
-    # end-to-end through the public API with host buffers
-    e2e = None if args.no_e2e else run_e2e(args, boba, torch, dev, stream, src_h, dst_h, m, n,
-                                           world)
+    if oracle_ex is not None:
+        oracle_ex.shutdown(wait=True, cancel_futures=True)
+        oracle_ex = None
 
     serving = None
     if args.serve and world == 1:
@@ -492,8 +498,6 @@ def run_ours(args):
         del src_h, dst_h
         batched = run_batched(args, boba, torch, dev, stream, flush, n_batch=args.batch_graphs)
 
-    if oracle_ex is not None:
-        oracle_ex.shutdown(wait=True, cancel_futures=True)
     result = {
         "metric": METRIC, "value": round(value, 3),
         "value_hbm_frac": reorder_roof["frac"], "unit": "Gedges/s", "n_gpus": world,
