@@ -9,8 +9,10 @@
 //   * a scheduler thread admits waiting requests in arrival order whenever a
 //     slot is free and the pool has room, so requests that arrive while others
 //     are on the GPU join as soon as memory frees up;
-//   * the requests admitted together form a wave: their graphs are packed and
-//     reordered by one boba_reorder_batched launch; each request then runs its
+//   * the requests admitted together form a wave (up to kWaveEdges edges):
+//     their graphs are copied in on a copy stream, packed, and reordered by
+//     one boba_reorder_batched launch, so the next wave's copies overlap this
+//     wave's compute; each request then runs its
 //     CSR build, SpMV iterations and copy back on its own stream, so waves and
 //     requests overlap on the device and a small request is not held back by
 //     a large one;
@@ -36,6 +38,10 @@ namespace boba {
 namespace {
 
 using Clock = std::chrono::steady_clock;
+
+// Edges above which a wave takes no further request (a request larger than
+// this forms a wave of its own).
+constexpr int64_t kWaveEdges = 1ll << 26;
 
 // First-fit allocator over one device region (host bookkeeping only).
 class DevicePool {
@@ -188,6 +194,7 @@ struct Server {
     std::vector<cudaStream_t> streams;
     size_t next_stream = 0;
     cudaStream_t wave_stream = nullptr;
+    cudaStream_t copy_stream = nullptr;       // a wave's input copies, ahead of its reorder
     boba_status_t error = BOBA_OK;
 
     void run();
@@ -238,16 +245,23 @@ bool Server::launch_wave(std::vector<Request *> &rs)
         r->spmv_ws = p + c.take(r->spmv_ws_bytes);
         r->wave = W;
     }
-    // inputs of the wave, packed
-    cudaStream_t ws = wave_stream;
+    // inputs of the wave, packed, on the copy stream: the next wave's copies
+    // then run while this wave's reorder and its requests compute
+    cudaStream_t cs = copy_stream;
     for (Request *r : rs) {
         if (r->m > 0) {
-            cudaMemcpyAsync(src + r->packed_e, r->src_h, 4 * (size_t)r->m, cudaMemcpyHostToDevice, ws);
-            cudaMemcpyAsync(dst + r->packed_e, r->dst_h, 4 * (size_t)r->m, cudaMemcpyHostToDevice, ws);
+            cudaMemcpyAsync(src + r->packed_e, r->src_h, 4 * (size_t)r->m, cudaMemcpyHostToDevice, cs);
+            cudaMemcpyAsync(dst + r->packed_e, r->dst_h, 4 * (size_t)r->m, cudaMemcpyHostToDevice, cs);
         }
     }
-    cudaMemcpyAsync(eo, W->eoff.data(), 8 * (size_t)(G + 1), cudaMemcpyHostToDevice, ws);
-    cudaMemcpyAsync(vo, W->voff.data(), 8 * (size_t)(G + 1), cudaMemcpyHostToDevice, ws);
+    cudaMemcpyAsync(eo, W->eoff.data(), 8 * (size_t)(G + 1), cudaMemcpyHostToDevice, cs);
+    cudaMemcpyAsync(vo, W->voff.data(), 8 * (size_t)(G + 1), cudaMemcpyHostToDevice, cs);
+    cudaEvent_t landed;
+    cudaEventCreateWithFlags(&landed, cudaEventDisableTiming);
+    cudaEventRecord(landed, cs);
+    cudaStream_t ws = wave_stream;
+    cudaStreamWaitEvent(ws, landed, 0);
+    cudaEventDestroy(landed);        // released once its work completes
     boba_status_t st = boba_reorder_batched(src, dst, eo, vo, G, mm, mn, tm, tn, perm, so, dout,
                                             bw, bws, ws);
     cudaEvent_t reordered;
@@ -316,13 +330,18 @@ void Server::run()
                 finished.push_back(r);
                 it = active.erase(it);
             }
-            // admission, in arrival order, while slots and memory allow
-            while (!pending.empty() && (int)(active.size() + wave.size()) < max_active) {
+            // admission, in arrival order, while slots and memory allow; a
+            // wave stops growing at kWaveEdges edges so that the next one's
+            // copies overlap its compute (it always takes one request)
+            int64_t wave_edges = 0;
+            while (!pending.empty() && (int)(active.size() + wave.size()) < max_active &&
+                   (wave.empty() || wave_edges + pending.front()->m <= kWaveEdges)) {
                 wave.push_back(pending.front());
                 if (wave_bytes(wave) + pool.used() > pool.size()) {
                     wave.pop_back();
                     break;
                 }
+                wave_edges += pending.front()->m;
                 pending.pop_front();
             }
             if (!wave.empty()) {
@@ -374,6 +393,7 @@ boba_server_t *boba_server_create(size_t hbm_budget_bytes, int max_active, int s
         S->streams.push_back(s);
     }
     cudaStreamCreateWithFlags(&S->wave_stream, cudaStreamNonBlocking);
+    cudaStreamCreateWithFlags(&S->copy_stream, cudaStreamNonBlocking);
     cudaEventCreate(&S->epoch);
     cudaEventRecord(S->epoch, S->wave_stream);
     S->worker = std::thread([S] { S->run(); });
@@ -513,6 +533,7 @@ void boba_server_destroy(boba_server_t *h)
     for (Request *r : S->finished) delete r;
     for (cudaStream_t s : S->streams) cudaStreamDestroy(s);
     cudaStreamDestroy(S->wave_stream);
+    cudaStreamDestroy(S->copy_stream);
     cudaEventDestroy(S->epoch);
     delete S;
 }
