@@ -49,6 +49,15 @@ import numpy as np  # noqa: E402
 
 METRIC = ("BOBA reorder Gedges/s + % HBM roofline (plain vs batched); "
           "SpMV GB/s BOBA vs random")
+# The paper's own reorder times (Sec. 1.2.4, Sec. 5.3, Table 2), on an NVIDIA
+# V100 32 GB with CUDA 11.6; the paper times the permutation only.  Context
+# beside `perm_only`, not a target (other hardware, other inputs).
+PAPER_REPORTED = {
+    "hardware": "NVIDIA V100 32 GB (80 SMs), CUDA 11.6",
+    "what": "BOBA permutation (no edge rewrite), the datasets' native edge order",
+    "kron_g500-logn20": {"edges": 89_000_000, "ms": 17.0, "gedges_s": 5.2},
+    "arabic-2005": {"edges": 639_900_000, "ms": 224.0, "gedges_s": 2.9},
+}
 FALLBACK_HBM_GBS = 6800.0
 HBM_NOMINAL_GBS = 7900.0          # GB300 HBM3e nominal, reported beside the measured peak
 L2_FLUSH_BYTES = 512 << 20
@@ -514,6 +523,7 @@ def run_ours(args):
         "reorder_roofline": reorder_roof,
         "target": target,
         "perm_only": perm_only,
+        "paper_reported": PAPER_REPORTED,
         "spmv_rel_l2_vs_fp64": spmv_err,
         "gather_ceiling": gather,
         "lookup_roofline": lookup_roofline(gather),
