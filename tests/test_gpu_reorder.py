@@ -187,15 +187,22 @@ def test_full_size_bit_exact(boba, wname):
     each compared on the device with the oracle's arrays."""
     w = synth.WORKLOADS[wname]
     I, J = w.generate()
-    operm, olab = oracle.boba_perm(I, J, w.n)
-    oso, odo = oracle.relabel(I, J, olab, w.n)
+    every_variant_equals_oracle(boba, I, J, w.n, wname)
+
+
+def every_variant_equals_oracle(boba, I, J, n, what):
+    """The default launch configuration and every lookup-kernel variant,
+    each compared on the device with the oracle's perm, labels and edges."""
+    m = len(I)
+    operm, olab = oracle.boba_perm(I, J, n)
+    oso, odo = oracle.relabel(I, J, olab, n)
     src = torch.from_numpy(I).cuda()
     dst = torch.from_numpy(J).cuda()
     del I, J
     ref = [torch.from_numpy(a).cuda() for a in (operm, olab, oso, odo)]
     del operm, olab, oso, odo
-    perm = torch.empty(w.n, dtype=torch.int32, device="cuda")
-    lab = torch.empty(w.n, dtype=torch.int32, device="cuda")
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    lab = torch.empty(n, dtype=torch.int32, device="cuda")
     so, do = torch.empty_like(src), torch.empty_like(dst)
     lib = boba.load()
     cases = [(None, 0)] + [(boba.TUNE_FIRST, v) for v in range(1, N_LOOKUP_VARIANTS)] + \
@@ -204,16 +211,26 @@ def test_full_size_bit_exact(boba, wname):
         for fam, v in cases:
             boba.tune_reset()
             if fam is not None:
-                lib.boba_tune_set(fam, w.m, v)
+                lib.boba_tune_set(fam, m, v)
             for t in (perm, lab, so, do):
                 t.fill_(-7)
-            boba.reorder(src, dst, w.n, perm_out=perm, src_out=so, dst_out=do, label_out=lab)
+            boba.reorder(src, dst, n, perm_out=perm, src_out=so, dst_out=do, label_out=lab)
             boba.stream_status()
             for name, got, want in zip(("perm", "label", "src_out", "dst_out"),
                                        (perm, lab, so, do), ref):
-                assert torch.equal(got, want), (wname, fam, v, name)
+                assert torch.equal(got, want), (what, fam, v, name)
     finally:
         boba.tune_reset()
+
+
+@pytest.mark.slow
+def test_positions_beyond_2_31(boba):
+    """m = 3 * 2^29 edges: positions of I ++ J run to 3.2e9, beyond 2^31, so
+    keys use the full unsigned 32-bit range (below the 0xFFFFFFFF sentinel);
+    every launch variant bit-exact against the oracle."""
+    m = 3 << 29
+    I, J = synth.rmat(24, m, seed=0xB0BA0031)
+    every_variant_equals_oracle(boba, I, J, 1 << 24, "m=3*2^29")
 
 
 @pytest.mark.parametrize("shards", [1, 2, 3, 5])
