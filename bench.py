@@ -760,13 +760,16 @@ def run_batched(args, boba, torch, dev, stream, flush, n_batch=4096, seed=None):
 
     # every schedule of the batched call, each checked against the per-graph
     # outputs: 0 is the one persistent launch (8-block clusters, keys in
-    # distributed shared memory), 1..5 the split schedules (a persistent launch
+    # distributed shared memory), 1..8 the split schedules (a persistent launch
     # for the small graphs, six grid-wide phase launches for the large ones)
     sched = {}
     names = {0: "cluster: plan + one persistent launch", 1: "split, sliced first <= 8, relabel <= 1",
              2: "split, sliced first and relabel <= 8", 3: "split, sliced first <= 8, relabel <= 2",
-             4: "split, global phases", 5: "split, sliced first <= 3"}
-    for mode in range(6):
+             4: "split, global phases", 5: "split, sliced first <= 3",
+             6: "split as 1, global relabel in per-SM runs of 2^21 edges",
+             7: "split as 6, global first-occurrence in per-SM runs too",
+             8: "split as 7, sliced first <= 1"}
+    for mode in range(9):
         boba.boba_batched_set_mode(mode)
         need = boba.boba_reorder_batched_workspace_bytes(n_batch, max_m, max_n, E, V)
         if need > ws.numel():
@@ -821,7 +824,10 @@ def run_batched(args, boba, torch, dev, stream, flush, n_batch=4096, seed=None):
             "schedule": {0: "split, sliced first <= 8 slices, relabel <= 1", 1: "cluster",
                          2: "split, sliced first and relabel <= 8 slices",
                          3: "split, sliced first <= 8 slices, relabel <= 2",
-                         4: "split, global phases", 5: "split, sliced first <= 3 slices"}.get(
+                         4: "split, global phases", 5: "split, sliced first <= 3 slices",
+                         6: "split as 0, global relabel in per-SM runs",
+                         7: "split as 0, global first and relabel in per-SM runs",
+                         8: "split, sliced first and relabel <= 1, the rest in per-SM runs"}.get(
                 (tuned or {}).get("batched", 0)),
             "bit_identical": identical}
 

@@ -269,7 +269,11 @@ size_t boba_reorder_batched_workspace_bytes(int64_t G, int64_t max_m, int64_t ma
  * shared memory, one slice per CTA, each CTA streaming all of the graph's
  * endpoints, and larger graphs use the keys in global memory.  S for the two
  * phases: 1 (the default): 8 and 1; 2: 8 and 8; 3: 8 and 2; 4: none and
- * none; 5: 3 and none.  -1 = back to the default (the autotuned choice, or
+ * none; 5: 3 and none; 6: as 1, except that the global-memory relabel runs
+ * one CTA per SM, each claiming runs of 2^21 consecutive edges so that an
+ * SM's L1 serves one graph's labels at a time; 7: as 6, with the
+ * global-memory first-occurrence pass in such runs too; 8: as 7 with
+ * first-occurrence S = 1.  -1 = back to the default (the autotuned choice, or
  * the BOBA_BATCH_MODE environment variable, "cluster" or "split").  All give
  * identical results.  Process-wide; host only.
  */
@@ -542,7 +546,7 @@ boba_status_t boba_tune_reorder(const int32_t *src, const int32_t *dst, int64_t 
 /*
  * boba_tune_batched -- the same for the schedule of boba_reorder_batched
  * (variant 0: the default split schedule, boba_batched_set_mode 1; 1: the
- * cluster mode, set_mode 0; 2 .. 5: the split schedules of set_mode 2 .. 5),
+ * cluster mode, set_mode 0; 2 .. 8: the split schedules of set_mode 2 .. 8),
  * keyed by total_m.  A variant that needs more scratch than ws_bytes is
  * skipped.  An explicit boba_batched_set_mode overrides the tuned choice.
  */

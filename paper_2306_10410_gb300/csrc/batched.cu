@@ -53,7 +53,8 @@ constexpr size_t kDynSmem = (size_t)kKcap * 4;
 constexpr int kU = 8;                      // stream loads in flight per thread
 constexpr int64_t kSmallMaxM = 1ll << 21;  // split mode: graphs with more edges go to the phase path
 constexpr int kHdrItems = 0, kHdrLarge = 1, kHdrTicket = 2, kHdrValid = 3, kHdrScanTicket = 4,
-              kHdrEmitTicket = 5, kHdrSliceFirst = 6, kHdrSliceRelabel = 7;
+              kHdrEmitTicket = 5, kHdrSliceFirst = 6, kHdrSliceRelabel = 7, kHdrRunTicket = 8,
+              kHdrFirstRunTicket = 9;
 constexpr int kMaxSlices = 8;              // sliced large path: n <= kMaxSlices * kKcap
 
 // tiles of the phase-batched large-graph path
@@ -92,6 +93,10 @@ struct BatchArgs {
     // sliced large path: graphs of at most this many slices take the sliced
     // first-occurrence / relabel kernel, the others the global one (0: none)
     int first_smax, relabel_smax;
+    // the global first-occurrence pass / relabel claims runs of consecutive
+    // chunks, one CTA per SM (k_bl_first_runs, k_bl_relabel_runs), instead of
+    // striding over the chunks
+    bool first_runs, relabel_runs;
 };
 
 __device__ __forceinline__ int floor_log2_p1(int64_t x)   // floor(log2(x + 1)), x >= 0
@@ -142,6 +147,8 @@ __global__ void __launch_bounds__(1024) k_batch_plan(BatchArgs a)
         a.hdr[kHdrEmitTicket] = 0;
         a.hdr[kHdrSliceFirst] = 0;
         a.hdr[kHdrSliceRelabel] = 0;
+        a.hdr[kHdrRunTicket] = 0;
+        a.hdr[kHdrFirstRunTicket] = 0;
         for (int k = 0; k < 5; ++k) carry[k] = 0;
     }
     __syncthreads();
@@ -550,6 +557,102 @@ __global__ void __launch_bounds__(kLB) k_bl_first(BatchArgs a)
     }
 }
 
+// Locate chunk c of the table `tab` for one warp: lane 0 searches (from the
+// warp's previous graph, `hint`) and publishes the item in `slot`.
+__device__ __forceinline__ LargeItem warp_find(const BatchArgs &a, const uint32_t *tab, uint32_t L,
+                                               uint32_t c, LargeItem &slot, uint32_t &hint)
+{
+    if ((threadIdx.x & 31) == 0) {
+        uint32_t j = hint;
+        bool found = false;
+        for (int k = 0; k < 4 && j < L; ++k, ++j) {
+            if (__ldg(tab + j) > c) break;
+            if (c < __ldg(tab + j + 1)) { found = true; break; }
+        }
+        if (!found) j = find_graph(tab, L, c);
+        hint = j;
+        const uint32_t g = a.order[j];
+        slot.j = j;
+        slot.E0 = a.eoff[g];
+        slot.m = a.eoff[g + 1] - slot.E0;
+        slot.V0 = a.voff[g];
+        slot.n = a.voff[g + 1] - slot.V0;
+        slot.local = c - tab[j];
+    }
+    __syncwarp();
+    const LargeItem it = slot;
+    __syncwarp();                          // the slot is rewritten for the next chunk
+    return it;
+}
+
+// Runs of consecutive chunks for one CTA per SM: the block claims run r from
+// `ticket`; returns false once all `runs` are taken.
+__device__ __forceinline__ bool claim_run(uint32_t *ticket, uint32_t runs, uint32_t &s_run,
+                                          uint32_t &r)
+{
+    if (threadIdx.x == 0) s_run = atomicAdd(ticket, 1u);
+    __syncthreads();
+    r = s_run;
+    __syncthreads();                       // s_run is rewritten for the next run
+    return r < runs;
+}
+
+constexpr int kRunBlock = 1024;
+constexpr int kRunWarps = kRunBlock / 32;
+constexpr uint32_t kRunPosChunks = 128;          // 2 M positions per run
+
+// The global first-occurrence pass in runs (see k_bl_relabel_runs): an SM
+// works on one graph's key array at a time, so the filtering reads of keys
+// already lowered can hit its L1.  A filtering read that L1 serves may be
+// older than the key in L2; keys only decrease, so it is never below the
+// current key and at worst costs an atomicMin that changes nothing.
+__global__ void __launch_bounds__(kRunBlock, 1) k_bl_first_runs(BatchArgs a)
+{
+    __shared__ uint32_t s_run;
+    __shared__ LargeItem s_it[kRunWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t hint = 0;
+    const uint32_t L = a.hdr[kHdrLarge];
+    const uint32_t total = a.lg_pc[L];
+    const uint32_t runs = (total + kRunPosChunks - 1) / kRunPosChunks;
+    constexpr int U = 16;                       // positions per lane per round
+    constexpr int kRound = 32 * U;
+    static_assert(kPosChunk % kRound == 0, "a chunk is whole rounds of a warp");
+    uint32_t r;
+    while (claim_run(&a.hdr[kHdrFirstRunTicket], runs, s_run, r)) {
+        const uint32_t cend = min(total, (r + 1) * kRunPosChunks);
+        for (uint32_t c = r * kRunPosChunks + w; c < cend; c += kRunWarps) {
+            const LargeItem it = warp_find(a, a.lg_pc, L, c, s_it[w], hint);
+            if (cdiv(it.n, kKcap) <= a.first_smax) continue;      // done by the sliced kernel
+            const uint32_t nn = (uint32_t)it.n;
+            uint32_t *key = a.kl + (size_t)a.lg_vt[it.j] * kVtxTile;
+            const int64_t c0 = (int64_t)it.local * kPosChunk;
+            const int64_t p1 = min(c0 + (int64_t)kPosChunk, 2 * it.m);
+            for (int64_t base = c0; base < p1; base += kRound) {
+                int32_t v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t i = base + u * 32 + lane;
+                    v[u] = -1;
+                    if (i < p1)
+                        v[u] = i < it.m ? __ldcs(a.src + it.E0 + i)
+                                        : __ldcs(a.dst + it.E0 + (i - it.m));
+                }
+                uint32_t cur[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) cur[u] = (uint32_t)v[u] < nn ? key[v[u]] : 0u;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t i = base + u * 32 + lane;
+                    if (i >= p1) continue;
+                    if ((uint32_t)v[u] >= nn) raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
+                    else if (cur[u] > (uint32_t)i) atomicMin(&key[v[u]], (uint32_t)i);
+                }
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kLB) k_bl_mark(BatchArgs a)
 {
     __shared__ LargeItem s_it;
@@ -848,6 +951,67 @@ __global__ void __launch_bounds__(kBB, 1) k_bl_first_sliced(BatchArgs a)
     }
 }
 
+// The global relabel with the work claimed in runs of kRunChunks consecutive
+// chunks by one 1024-thread CTA per SM.  A run lies mostly inside one graph, so
+// while an SM works through it its L1 holds much of that graph's label array
+// (up to 1 MB for the graphs of this path): a label lookup that hits L1 sends
+// no request to L2, and the lookups are bound by that request rate.  In the
+// grid-stride kernel above, an SM's blocks work on unrelated graphs at once.
+// A ticket hands out the runs, so the SMs stay balanced.  Inside a run each
+// warp takes every 32nd chunk on its own, with no block-wide barrier.
+constexpr uint32_t kRunChunks = 256;            // 2 M edges per run
+
+__global__ void __launch_bounds__(kRunBlock, 1) k_bl_relabel_runs(BatchArgs a)
+{
+    __shared__ uint32_t s_run;
+    __shared__ LargeItem s_it[kRunWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t hint = 0;
+    const uint32_t L = a.hdr[kHdrLarge];
+    const uint32_t total = a.lg_ec[L];
+    const uint32_t runs = (total + kRunChunks - 1) / kRunChunks;
+    constexpr int U = 8;                        // edges per lane per round
+    constexpr int kRound = 32 * U;
+    static_assert(kEdgeChunk % kRound == 0, "a chunk is whole rounds of a warp");
+    uint32_t r;
+    while (claim_run(&a.hdr[kHdrRunTicket], runs, s_run, r)) {
+        const uint32_t cend = min(total, (r + 1) * kRunChunks);
+        for (uint32_t c = r * kRunChunks + w; c < cend; c += kRunWarps) {
+            const LargeItem it = warp_find(a, a.lg_ec, L, c, s_it[w], hint);
+            if (cdiv(it.n, kKcap) <= a.relabel_smax) continue;    // done by the sliced kernel
+            const uint32_t nn = (uint32_t)it.n;
+            const uint32_t *lab = a.kl + (size_t)a.lg_vt[it.j] * kVtxTile;
+            const int64_t c0 = (int64_t)it.local * kEdgeChunk;
+            const int64_t c1 = min(c0 + (int64_t)kEdgeChunk, it.m);
+            for (int64_t base = c0; base < c1; base += kRound) {
+                int32_t sv[U], dv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t e = base + u * 32 + lane;
+                    sv[u] = dv[u] = -1;
+                    if (e < c1) {
+                        sv[u] = __ldcs(a.src + it.E0 + e);
+                        dv[u] = __ldcs(a.dst + it.E0 + e);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    sv[u] = (uint32_t)sv[u] < nn ? (int32_t)__ldg(lab + sv[u]) : -1;
+                    dv[u] = (uint32_t)dv[u] < nn ? (int32_t)__ldg(lab + dv[u]) : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int64_t e = base + u * 32 + lane;
+                    if (e >= c1) continue;
+                    if (sv[u] < 0 || dv[u] < 0) raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
+                    __stcs(a.so + it.E0 + e, sv[u]);
+                    __stcs(a.dout + it.E0 + e, dv[u]);
+                }
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kBB, 1) k_bl_relabel_sliced(BatchArgs a)
 {
     extern __shared__ uint32_t s_lab[];    // kKcap
@@ -972,7 +1136,10 @@ int batch_mode(int64_t total_m)
 //   1: fs 8, rs 1 (the default: measured best on the 4096-graph batch; a
 //      one-slice graph relabels without redundant streams or partial writes)
 //   2: fs 8, rs 8     3: fs 8, rs 2     4: global phases only     5: fs 3, rs 0
-void batch_slices(int64_t total_m, int &fs, int &rs)
+//   6: as 1, with the global relabel claiming runs of chunks per SM
+//   7: as 6, with the global first-occurrence pass in runs too
+//   8: as 7 with fs 1
+void batch_slices(int64_t total_m, int &fs, int &rs, bool &first_runs, bool &runs)
 {
     int sched = g_mode_override;
     if (sched < 0) {
@@ -980,10 +1147,14 @@ void batch_slices(int64_t total_m, int &fs, int &rs)
         sched = v == 0 ? 1 : v == 1 ? 0 : v;
     }
     fs = rs = 0;
+    first_runs = runs = false;
     if (sched == 1) { fs = kMaxSlices; rs = 1; }
     else if (sched == 2) { fs = kMaxSlices; rs = kMaxSlices; }
     else if (sched == 3) { fs = kMaxSlices; rs = 2; }
     else if (sched == 5) { fs = 3; }
+    else if (sched == 6) { fs = kMaxSlices; rs = 1; runs = true; }
+    else if (sched == 7) { fs = kMaxSlices; rs = 1; first_runs = runs = true; }
+    else if (sched == 8) { fs = 1; rs = 1; first_runs = runs = true; }
 }
 
 struct BatchLayout {
@@ -1096,7 +1267,7 @@ extern "C" boba_status_t boba_reorder_batched(const int32_t *src, const int32_t 
         a.lts_emit = reinterpret_cast<uint64_t *>(b + L.lts_emit);
         a.lts_scan_cap = L.lwt_cap;
         a.lts_emit_cap = L.lvt_cap;
-        batch_slices(total_m, a.first_smax, a.relabel_smax);
+        batch_slices(total_m, a.first_smax, a.relabel_smax, a.first_runs, a.relabel_runs);
     }
     BOBA_TIMED("batch.plan", stream, k_batch_plan<<<1, 1024, 0, stream>>>(a));
     if (mode == kBatchCluster) {
@@ -1111,24 +1282,34 @@ extern "C" boba_status_t boba_reorder_batched(const int32_t *src, const int32_t 
         if (a.first_smax > 0)
             BOBA_TIMED("batch.large.first", stream,
                        k_bl_first_sliced<<<bd->grid_small, kBB, kDynSmem, stream>>>(a));
-        if (max_n > (int64_t)a.first_smax * kKcap)
-            BOBA_TIMED("batch.large.first", stream, k_bl_first<<<gl, kLB, 0, stream>>>(a));
+        if (max_n > (int64_t)a.first_smax * kKcap) {
+            if (a.first_runs)
+                BOBA_TIMED("batch.large.first", stream,
+                           k_bl_first_runs<<<bd->sms, kRunBlock, 0, stream>>>(a));
+            else
+                BOBA_TIMED("batch.large.first", stream, k_bl_first<<<gl, kLB, 0, stream>>>(a));
+        }
         BOBA_TIMED("batch.large.mark", stream, k_bl_mark<<<gl, kLB, 0, stream>>>(a));
         BOBA_TIMED("batch.large.scan", stream, k_bl_scan<<<gl, kLB, 0, stream>>>(a));
         BOBA_TIMED("batch.large.emit", stream, k_bl_emit<<<gl, kLB, 0, stream>>>(a));
         if (a.relabel_smax > 0)
             BOBA_TIMED("batch.large.relabel", stream,
                        k_bl_relabel_sliced<<<bd->grid_small, kBB, kDynSmem, stream>>>(a));
-        if (max_n > (int64_t)a.relabel_smax * kKcap)
-            BOBA_TIMED("batch.large.relabel", stream, k_bl_relabel<<<gl, kLB, 0, stream>>>(a));
+        if (max_n > (int64_t)a.relabel_smax * kKcap) {
+            if (a.relabel_runs)
+                BOBA_TIMED("batch.large.relabel", stream,
+                           k_bl_relabel_runs<<<bd->sms, kRunBlock, 0, stream>>>(a));
+            else
+                BOBA_TIMED("batch.large.relabel", stream, k_bl_relabel<<<gl, kLB, 0, stream>>>(a));
+        }
     }
     BOBA_LAUNCH_CHECK();
     return BOBA_OK;
 }
 
-// Selects the batched schedule explicitly: 0 cluster, 1 .. 5 split with the
+// Selects the batched schedule explicitly: 0 cluster, 1 .. 8 split with the
 // large-graph phases as batch_slices lists, -1 default.
 extern "C" void boba_batched_set_mode(int mode)
 {
-    g_mode_override = (mode >= 0 && mode <= 5) ? mode : -1;
+    g_mode_override = (mode >= 0 && mode <= 8) ? mode : -1;
 }

@@ -23,7 +23,9 @@ def boba():
 
 MODES = [pytest.param(0, id="cluster"), pytest.param(1, id="split"),
          pytest.param(2, id="sliced"), pytest.param(3, id="sliced_mixed"),
-         pytest.param(4, id="global"), pytest.param(5, id="sliced_small")]
+         pytest.param(4, id="global"), pytest.param(5, id="sliced_small"),
+         pytest.param(6, id="relabel_runs"), pytest.param(7, id="runs"),
+         pytest.param(8, id="runs_first")]
 
 
 def pack(graphs):
