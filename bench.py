@@ -766,7 +766,7 @@ def run_batched(args, boba, torch, dev, stream, flush, n_batch=4096, seed=None):
     names = {0: "cluster: plan + one persistent launch", 1: "split, sliced first <= 8, relabel <= 1",
              2: "split, sliced first and relabel <= 8", 3: "split, sliced first <= 8, relabel <= 2",
              4: "split, global phases", 5: "split, sliced first <= 3",
-             6: "split as 1, global relabel in per-SM runs of 2^21 edges",
+             6: "split as 1, global relabel in per-SM runs of 2^21 edges (default)",
              7: "split as 6, global first-occurrence in per-SM runs too",
              8: "split as 7, sliced first <= 1"}
     for mode in range(9):
@@ -821,11 +821,12 @@ def run_batched(args, boba, torch, dev, stream, flush, n_batch=4096, seed=None):
             "kernels_ms": split,
             "schedules": sched,
             "cuda_graph_ms": t_graph,
-            "schedule": {0: "split, sliced first <= 8 slices, relabel <= 1", 1: "cluster",
+            "schedule": {0: "split, sliced first <= 8 slices, relabel <= 1, global relabel in "
+                            "per-SM runs", 1: "cluster",
                          2: "split, sliced first and relabel <= 8 slices",
                          3: "split, sliced first <= 8 slices, relabel <= 2",
                          4: "split, global phases", 5: "split, sliced first <= 3 slices",
-                         6: "split as 0, global relabel in per-SM runs",
+                         6: "split, sliced first <= 8 slices, relabel <= 1, grid-stride relabel",
                          7: "split as 0, global first and relabel in per-SM runs",
                          8: "split, sliced first and relabel <= 1, the rest in per-SM runs"}.get(
                 (tuned or {}).get("batched", 0)),

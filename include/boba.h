@@ -262,14 +262,14 @@ size_t boba_reorder_batched_workspace_bytes(int64_t G, int64_t max_m, int64_t ma
 /*
  * boba_batched_set_mode -- how boba_reorder_batched schedules graphs above
  * 55,296 vertices.  0 = on 8-CTA clusters with the keys in distributed shared
- * memory (one persistent cluster launch for everything).  1 .. 5 = all of
+ * memory (one persistent cluster launch for everything).  1 .. 8 = all of
  * them together, phase by phase, beside a persistent one-CTA-per-graph
  * launch for the smaller graphs; the first-occurrence and relabel phases of
  * a graph of up to S slices of 55,296 vertices keep its keys / labels in
  * shared memory, one slice per CTA, each CTA streaming all of the graph's
  * endpoints, and larger graphs use the keys in global memory.  S for the two
- * phases: 1 (the default): 8 and 1; 2: 8 and 8; 3: 8 and 2; 4: none and
- * none; 5: 3 and none; 6: as 1, except that the global-memory relabel runs
+ * phases: 1: 8 and 1; 2: 8 and 8; 3: 8 and 2; 4: none and none; 5: 3 and
+ * none; 6 (the default): as 1, except that the global-memory relabel runs
  * one CTA per SM, each claiming runs of 2^21 consecutive edges so that an
  * SM's L1 serves one graph's labels at a time; 7: as 6, with the
  * global-memory first-occurrence pass in such runs too; 8: as 7 with
@@ -545,8 +545,9 @@ boba_status_t boba_tune_reorder(const int32_t *src, const int32_t *dst, int64_t 
 
 /*
  * boba_tune_batched -- the same for the schedule of boba_reorder_batched
- * (variant 0: the default split schedule, boba_batched_set_mode 1; 1: the
- * cluster mode, set_mode 0; 2 .. 8: the split schedules of set_mode 2 .. 8),
+ * (variant 0: the default split schedule, boba_batched_set_mode 6; 1: the
+ * cluster mode, set_mode 0; 6: set_mode 1; 2 .. 5, 7, 8: the split schedules
+ * of the same set_mode),
  * keyed by total_m.  A variant that needs more scratch than ws_bytes is
  * skipped.  An explicit boba_batched_set_mode overrides the tuned choice.
  */

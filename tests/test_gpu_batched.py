@@ -137,6 +137,39 @@ def test_bad_offsets_are_skipped_and_reported(boba, mode):
     assert np.all(p.cpu().numpy()[100:200] == -9)                       # graph 1 skipped
 
 
+@pytest.mark.parametrize("mode", MODES)
+def test_out_of_range_ids_reported(boba, mode):
+    """An endpoint outside [0, n) of its own graph raises BOBA_ERR_ID_OUT_OF_RANGE
+    and is written as -1; the other graphs of the batch come out unchanged.
+    Graph 0 runs in one CTA; graph 1 has three slices, its bad IDs in
+    several of them and at both ends of its endpoint stream."""
+    boba.boba_batched_set_mode(mode)
+    graphs = []
+    for n, m, seed in ((3000, 40_000, 31), (2 * KCAP + 100, 600_000, 32),
+                       (3 * KCAP + 7, 900_000, 33), (5000, 60_000, 34)):
+        I, J = synth.rmat(int(np.ceil(np.log2(n))), m, seed=seed, n=n)
+        graphs.append((I.copy(), J.copy(), n))
+    n0, n1 = graphs[0][2], graphs[1][2]
+    m1 = len(graphs[1][0])
+    bad = {0: [(0, 17, n0), (1, 5, -1)],
+           1: [(0, 0, n1 + 7), (1, 999, -3), (0, 400_000, 1 << 30), (1, m1 - 1, n1)]}
+    for g, items in bad.items():
+        for side, e, v in items:
+            graphs[g][side][e] = v
+    src, dst, eo, vo = pack(graphs)
+    perm, so, do = boba.reorder_batched(torch.from_numpy(src).cuda(), torch.from_numpy(dst).cuda(),
+                                        torch.from_numpy(eo).cuda(), torch.from_numpy(vo).cuda())
+    with pytest.raises(boba.BobaError) as e:
+        boba.stream_status()
+    assert e.value.code == 2
+    so, do = so.cpu().numpy(), do.cpu().numpy()
+    for g, items in bad.items():
+        for side, e_, _ in items:
+            assert (so if side == 0 else do)[eo[g] + e_] == -1, (g, side, e_)
+    check_against_oracle(graphs, perm.cpu().numpy(), so, do, eo, vo, which=[2, 3])
+    boba.stream_status()                          # the word was cleared
+
+
 def test_size_limits(boba):
     z = torch.zeros(8, dtype=torch.int64, device="cuda")
     i = torch.zeros(8, dtype=torch.int32, device="cuda")
