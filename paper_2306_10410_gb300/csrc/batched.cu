@@ -910,6 +910,82 @@ __device__ __forceinline__ void stream_block(const int32_t *__restrict__ X, int6
     if (t0 + threadIdx.x < mm) f(__ldcg(X + t0 + threadIdx.x), p0 + t0 + threadIdx.x);
 }
 
+// The sliced first-occurrence visit of X[0, m) at positions pos0 + e, for the
+// slice [base, base + cnt) whose keys are in s_keys.  Per group of
+// kFirstSliceG int4 loads, every element's filtering read of its key is issued
+// before any atomicMin: an atomic may alias a later read, so interleaving them
+// would serialise each element on the shared-memory latency.  A key read early
+// may be stale; keys only decrease, so it is never below the current key and
+// at worst costs an atomicMin that changes nothing.  With CHECK, vmax takes
+// the largest ID seen (as unsigned, so a negative ID counts as huge).
+constexpr int kFirstSliceU = 6;
+constexpr int kFirstSliceG = 2;                 // int4 loads per read-then-update group
+static_assert(kFirstSliceU % kFirstSliceG == 0, "whole groups");
+
+__device__ __forceinline__ int32_t lane_of(const int4 &q, int j)
+{
+    return j == 0 ? q.x : j == 1 ? q.y : j == 2 ? q.z : q.w;
+}
+
+template <bool CHECK>
+__device__ __forceinline__ void first_slice_stream(const int32_t *__restrict__ X, int64_t m,
+                                                   int64_t pos0, uint32_t base, uint32_t cnt,
+                                                   uint32_t *s_keys, uint32_t &vmax)
+{
+    const uint32_t mm = (uint32_t)m, p0 = (uint32_t)pos0;
+    auto one = [&](int32_t v, uint32_t p) {
+        const uint32_t u = (uint32_t)v - base;
+        const bool own = u < cnt;
+        const uint32_t cur = own ? s_keys[u] : 0u;
+        if (own && cur > p) atomicMin(&s_keys[u], p);
+        if constexpr (CHECK) vmax = max(vmax, (uint32_t)v);
+    };
+    uint32_t head = ((16u - ((uint32_t)(uintptr_t)X & 15u)) & 15u) >> 2;
+    if (head > mm) head = mm;
+    if (threadIdx.x < head) one(__ldcg(X + threadIdx.x), p0 + threadIdx.x);
+    const int4 *X4 = reinterpret_cast<const int4 *>(X + head);
+    const uint32_t q = (mm - head) >> 2;
+    const uint32_t pb = p0 + head;
+    constexpr uint32_t step = (uint32_t)kBB * kFirstSliceU;
+    for (uint32_t b0 = threadIdx.x; b0 < q; b0 += step) {
+        int4 w[kFirstSliceU];
+#pragma unroll
+        for (int u = 0; u < kFirstSliceU; ++u) {
+            const uint32_t k = b0 + (uint32_t)u * kBB;
+            // -1 beyond the end: outside every slice, and not counted in vmax
+            w[u] = k < q ? __ldcg(X4 + k) : make_int4(-1, -1, -1, -1);   // kept in L2 for the sibling slices
+        }
+        // the filtering reads, then the atomics, for kFirstSliceG of the
+        // loads at a time (registers: the reads of all of them would not fit)
+#pragma unroll
+        for (int h = 0; h < kFirstSliceU; h += kFirstSliceG) {
+            uint32_t cur[4 * kFirstSliceG];
+#pragma unroll
+            for (int u = h; u < h + kFirstSliceG; ++u) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t x = (uint32_t)lane_of(w[u], j) - base;
+                    cur[4 * (u - h) + j] = x < cnt ? s_keys[x] : 0u;
+                    if constexpr (CHECK)
+                        if (b0 + (uint32_t)u * kBB < q) vmax = max(vmax, (uint32_t)lane_of(w[u], j));
+                }
+            }
+#pragma unroll
+            for (int u = h; u < h + kFirstSliceG; ++u) {
+                const uint32_t p = pb + 4u * (b0 + (uint32_t)u * kBB);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t x = (uint32_t)lane_of(w[u], j) - base;
+                    if (x < cnt && cur[4 * (u - h) + j] > p + (uint32_t)j)
+                        atomicMin(&s_keys[x], p + (uint32_t)j);
+                }
+            }
+        }
+    }
+    const uint32_t t0 = head + 4u * q;
+    if (t0 + threadIdx.x < mm) one(__ldcg(X + t0 + threadIdx.x), p0 + t0 + threadIdx.x);
+}
+
 __global__ void __launch_bounds__(kBB, 1) k_bl_first_sliced(BatchArgs a)
 {
     extern __shared__ uint32_t s_keys[];   // kKcap
@@ -930,20 +1006,19 @@ __global__ void __launch_bounds__(kBB, 1) k_bl_first_sliced(BatchArgs a)
         const uint32_t cnt = (uint32_t)min((int64_t)kKcap, it.n - base);
         for (uint32_t i = threadIdx.x; i < cnt; i += kBB) s_keys[i] = kSent;
         __syncthreads();
-        const uint32_t nn = (uint32_t)it.n;
-        bool bad = false;
         // few branches per element: most endpoints belong to other slices,
-        // and divergent branches cost more here than the predicated load
-        auto visit = [&](int32_t v, uint32_t p) {
-            const uint32_t u = (uint32_t)v - base;
-            const bool own = u < cnt;
-            const uint32_t cur = own ? s_keys[u] : 0u;
-            if (own && cur > p) atomicMin(&s_keys[u], p);
-            bad |= (uint32_t)v >= nn;
-        };
-        stream_block(a.src + it.E0, it.m, 0, visit);          // positions 0 .. m-1
-        stream_block(a.dst + it.E0, it.m, it.m, visit);       // positions m .. 2m-1
-        if (bad && it.local == 0) raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
+        // and divergent branches cost more here than the predicated load.
+        // An ID outside [0, n) is in no slice, so it is never written; the
+        // task of slice 0 alone looks for one, as the largest ID it sees.
+        uint32_t vmax = 0;
+        if (it.local == 0) {
+            first_slice_stream<true>(a.src + it.E0, it.m, 0, base, cnt, s_keys, vmax);
+            first_slice_stream<true>(a.dst + it.E0, it.m, it.m, base, cnt, s_keys, vmax);
+            if (vmax >= (uint32_t)it.n) raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
+        } else {
+            first_slice_stream<false>(a.src + it.E0, it.m, 0, base, cnt, s_keys, vmax);
+            first_slice_stream<false>(a.dst + it.E0, it.m, it.m, base, cnt, s_keys, vmax);
+        }
         __syncthreads();
         uint32_t *key = a.kl + (size_t)a.lg_vt[it.j] * kVtxTile + base;
         for (uint32_t i = threadIdx.x; i < cnt; i += kBB) key[i] = s_keys[i];
@@ -1122,7 +1197,7 @@ const BatchDevice *batch_device()
 int batch_mode(int64_t total_m)
 {
     if (g_mode_override >= 0) return g_mode_override == 0 ? kBatchCluster : kBatchSplit;
-    const int v = tuned_variant(kTuneBatched, total_m);      // 0 split, 1 cluster, 2 split+sliced
+    const int v = tuned_variant(kTuneBatched, total_m);      // 1 cluster, the others split
     if (v == 1) return kBatchCluster;
     const char *e = getenv("BOBA_BATCH_MODE");
     if (v == 0 && e && strcmp(e, "cluster") == 0) return kBatchCluster;
@@ -1132,11 +1207,12 @@ int batch_mode(int64_t total_m)
 // Split mode: up to how many slices a large graph takes the sliced
 // first-occurrence (fs) and relabel (rs) kernel instead of the global one.
 // Schedules (the numbers of boba_batched_set_mode; the tuner's variants are
-// the same except that its 0 is schedule 1 and its 1 is schedule 0):
-//   1: fs 8, rs 1 (the default: measured best on the 4096-graph batch; a
-//      one-slice graph relabels without redundant streams or partial writes)
+// the same except that its 0 is schedule 6, its 1 schedule 0, its 6 schedule 1):
+//   1: fs 8, rs 1 (a one-slice graph relabels without redundant streams or
+//      partial writes; the global relabel strides over the chunks)
 //   2: fs 8, rs 8     3: fs 8, rs 2     4: global phases only     5: fs 3, rs 0
-//   6: as 1, with the global relabel claiming runs of chunks per SM
+//   6: as 1, with the global relabel claiming runs of chunks per SM (the
+//      default: measured best on the 4096-graph batch, 28.1 ms against 31.1)
 //   7: as 6, with the global first-occurrence pass in runs too
 //   8: as 7 with fs 1
 void batch_slices(int64_t total_m, int &fs, int &rs, bool &first_runs, bool &runs)
@@ -1144,7 +1220,7 @@ void batch_slices(int64_t total_m, int &fs, int &rs, bool &first_runs, bool &run
     int sched = g_mode_override;
     if (sched < 0) {
         const int v = tuned_variant(kTuneBatched, total_m);
-        sched = v == 0 ? 1 : v == 1 ? 0 : v;
+        sched = v == 0 ? 6 : v == 1 ? 0 : v == 6 ? 1 : v;
     }
     fs = rs = 0;
     first_runs = runs = false;
