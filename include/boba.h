@@ -562,7 +562,10 @@ boba_status_t boba_tune_batched(const int32_t *src, const int32_t *dst, const in
  * chosen from nnz / n_rows; 1..4: 4, 8, 16, 32 lanes per row; 5..8: merge-path
  * decomposition over row ends and nonzeros with 256x8, 256x12, 512x8, 128x16
  * threads x items per tile; 9..13: merge path with a 64 KB or 32 KB cap on the
- * shared-memory carve-out, leaving the rest to L1 for the x gathers), keyed
+ * shared-memory carve-out, leaving the rest to L1 for the x gathers; 14:
+ * 256x12 with the 64 KB cap, gathering x[0, 65536) with an L1 evict-last
+ * hint: on a BOBA order the most frequent columns have the smallest
+ * labels), keyed
  * by nnz.  The variants sum in different orders, so their results may differ
  * in the last bits; each is deterministic.  A variant whose y is further than
  * 1e-5 (relative L2) from variant 0's is never chosen.  Allocates a reference

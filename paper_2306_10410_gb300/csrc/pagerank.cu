@@ -237,7 +237,7 @@ extern "C" boba_status_t boba_pagerank(const int64_t *row_ptr, const int32_t *co
                                                             max_iters, st, part, iters_out,
                                                             residual_out));
     int variant = tuned_variant(kTuneSpmv, nnz);
-    if (variant < 5 || variant > 13) variant = 5;
+    if (variant < 5 || variant > 14) variant = 5;
     if (max_iters > 0)
         merge_path_partition(row_ptr, n, nnz, merge_path_items(variant), mp_part, s);
     for (int64_t t = 0; t < max_iters; ++t) {

@@ -227,14 +227,29 @@ struct MpSmem {
     KV s_warp[MB / 32];
 };
 
+// A gather of x that asks L1 to keep the line (evict-last).  On a BOBA order
+// the vertices that appear most often take the smallest labels, so the first
+// entries of x are gathered far more often than the rest (R-MAT 24, 2^28
+// edges: x[0, 65536) serves 32 % of the nonzeros); marking their lines helps
+// them stay in L1 against the one-off lines of the other gathers.
+__device__ __forceinline__ float ld_x_keep(const float *p)
+{
+    float v;
+    asm("ld.global.nc.L1::evict_last.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
 // One tile of the merge path: the tile's rows and nonzeros split evenly over
-// the MB threads (MI path items each).
-template <int MB, int MI>
+// the MB threads (MI path items each).  With HOT, columns below `hot` are
+// gathered by ld_x_keep.  Both loads are issued by every lane, each lane
+// pointing the one it does not need at x[0]: a per-lane branch between two
+// loads would serialise them and stall the gathers in flight.
+template <int MB, int MI, bool HOT = false>
 __device__ __forceinline__ void mp_tile(
     int64_t tile, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
     const float *__restrict__ val, const float *__restrict__ x, float *__restrict__ y,
     const int2 *__restrict__ part, int32_t *__restrict__ carry_row, float *__restrict__ carry_val,
-    MpSmem<MB, MI> &sm)
+    MpSmem<MB, MI> &sm, int32_t hot = 0)
 {
     constexpr int kMpBlock = MB, kMpItems = MI;
     auto P = [](int j) { return j + (j >> 5); };
@@ -251,7 +266,19 @@ __device__ __forceinline__ void mp_tile(
 #pragma unroll
     for (int u = 0; u < kMpItems; ++u) {
         const int j = u * kMpBlock + threadIdx.x;
-        if (j < nnzt) s_prod[P(j)] = __ldcs(val + y0 + j) * __ldg(x + __ldcs(col + y0 + j));
+        if (j < nnzt) {
+            const int32_t c = __ldcs(col + y0 + j);
+            float xv;
+            if constexpr (HOT) {
+                const bool h = c < hot;
+                const float a = ld_x_keep(x + (h ? c : 0));
+                const float b = __ldg(x + (h ? 0 : c));
+                xv = h ? a : b;
+            } else {
+                xv = __ldg(x + c);
+            }
+            s_prod[P(j)] = __ldcs(val + y0 + j) * xv;
+        }
     }
     __syncthreads();
     // this thread's split inside the tile
@@ -327,17 +354,17 @@ __device__ __forceinline__ void mp_tile(
 }
 
 // CARVE only makes separate instances, so that a shared-memory carve-out set
-// for one variant does not apply to the others.
-template <int MB, int MI, int CARVE = 0>
+// for one variant does not apply to the others.  HOT: see mp_tile.
+template <int MB, int MI, int CARVE = 0, bool HOT = false>
 __global__ void __launch_bounds__(MB) k_mp_spmv(
     const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col,
     const float *__restrict__ val, const float *__restrict__ x, float *__restrict__ y, int64_t n,
     int64_t nnz, const int2 *__restrict__ part, int32_t *__restrict__ carry_row,
-    float *__restrict__ carry_val, const uint32_t *skip)
+    float *__restrict__ carry_val, const uint32_t *skip, int32_t hot)
 {
     if (skip != nullptr && *skip != 0) return;       // an iterative caller has converged
     __shared__ MpSmem<MB, MI> sm;
-    mp_tile<MB, MI>(blockIdx.x, row_ptr, col, val, x, y, part, carry_row, carry_val, sm);
+    mp_tile<MB, MI, HOT>(blockIdx.x, row_ptr, col, val, x, y, part, carry_row, carry_val, sm, hot);
 }
 
 // y[r] += the carries of the tiles that ended inside row r, in tile order.
@@ -373,19 +400,20 @@ void launch_rows(const int64_t *row_ptr, const int32_t *col, const float *val, c
 
 }  // namespace
 
-// Merge-path shapes of the tuned SpMV variants 5 .. 13: threads per block,
-// path items per thread, and the cap on the shared-memory carve-out in KB
-// (0: the default, which maximises resident blocks).  A smaller carve-out
-// trades resident warps for L1, which holds the hot x entries.
+// Merge-path shapes of the tuned SpMV variants 5 .. 14: threads per block,
+// path items per thread, the cap on the shared-memory carve-out in KB (0: the
+// default, which maximises resident blocks), and the hot prefix of x in
+// entries (0: none; see mp_tile).  A smaller carve-out trades resident warps
+// for L1, which holds the hot x entries.
 struct MpShape {
-    int block, items, carve_kb;
+    int block, items, carve_kb, hot;
 };
 constexpr MpShape kMpShapes[] = {
-    {256, 8, 0}, {256, 12, 0}, {512, 8, 0}, {128, 16, 0},          // 5 .. 8
-    {256, 8, 64}, {256, 8, 32}, {256, 12, 64}, {512, 8, 64},       // 9 .. 12
-    {256, 16, 64},                                                 // 13
+    {256, 8, 0, 0}, {256, 12, 0, 0}, {512, 8, 0, 0}, {128, 16, 0, 0},          // 5 .. 8
+    {256, 8, 64, 0}, {256, 8, 32, 0}, {256, 12, 64, 0}, {512, 8, 64, 0},       // 9 .. 12
+    {256, 16, 64, 0}, {256, 12, 64, 65536},                                    // 13 .. 14
 };
-constexpr int kMpFirst = 5, kMpLast = 13;
+constexpr int kMpFirst = 5, kMpLast = 14;
 
 MpShape mp_shape(int variant)
 {
@@ -401,24 +429,26 @@ int merge_path_items(int variant)
 
 namespace {
 
-// One launch of k_mp_spmv<MB, MI, CARVE>; with a carve-out cap the attribute
-// is set on that instance only, once per device.
-template <int MB, int MI, int CARVE>
-void launch_mp(int carve_kb, const int64_t *row_ptr, const int32_t *col, const float *val,
-               const float *x, float *y, int64_t n, int64_t nnz, const int2 *part, int32_t *crow,
-               float *cval, const uint32_t *skip, int64_t tiles, cudaStream_t stream)
+// One launch of k_mp_spmv<MB, MI, CARVE, HOT>; with a carve-out cap the
+// attribute is set on that instance only, once per device.
+template <int MB, int MI, int CARVE, bool HOT = false>
+void launch_mp(int carve_kb, int hot, const int64_t *row_ptr, const int32_t *col,
+               const float *val, const float *x, float *y, int64_t n, int64_t nnz,
+               const int2 *part, int32_t *crow, float *cval, const uint32_t *skip, int64_t tiles,
+               cudaStream_t stream)
 {
     static std::atomic<uint64_t> done{0};          // devices whose attribute is set
     int dev = 0;
     cudaGetDevice(&dev);
     const uint64_t bit = 1ull << (dev & 63);
     if (carve_kb > 0 && (done.load() & bit) == 0) {
-        cudaFuncSetAttribute((const void *)k_mp_spmv<MB, MI, CARVE>,
+        cudaFuncSetAttribute((const void *)k_mp_spmv<MB, MI, CARVE, HOT>,
                              cudaFuncAttributePreferredSharedMemoryCarveout, carve_kb * 100 / 228);
         done.fetch_or(bit);
     }
-    BOBA_TIMED("spmv", stream, k_mp_spmv<MB, MI, CARVE><<<(unsigned)tiles, MB, 0, stream>>>(
-                                   row_ptr, col, val, x, y, n, nnz, part, crow, cval, skip));
+    BOBA_TIMED("spmv", stream,
+               k_mp_spmv<MB, MI, CARVE, HOT><<<(unsigned)tiles, MB, 0, stream>>>(
+                   row_ptr, col, val, x, y, n, nnz, part, crow, cval, skip, (int32_t)hot));
 }
 
 }  // namespace
@@ -439,21 +469,23 @@ void merge_path_multiply(int variant, const int64_t *row_ptr, const int32_t *col
     if (variant < kMpFirst || variant > kMpLast) variant = kMpFirst;
     const int64_t tiles = cdiv(n + nnz, merge_path_items(variant));
     const int kb = mp_shape(variant).carve_kb;
-#define BOBA_MP(V, MB, MI, C)                                                                  \
+    const int hot = (int)(mp_shape(variant).hot < n ? mp_shape(variant).hot : n);   // within x
+#define BOBA_MP(V, MB, MI, C, H)                                                               \
     case V:                                                                                    \
-        launch_mp<MB, MI, C>(kb, row_ptr, col, val, x, y, n, nnz, part, crow, cval, skip, tiles, \
-                             stream);                                                          \
+        launch_mp<MB, MI, C, H>(kb, hot, row_ptr, col, val, x, y, n, nnz, part, crow, cval,    \
+                                skip, tiles, stream);                                          \
         break;
     switch (variant) {
-        BOBA_MP(5, 256, 8, 0)
-        BOBA_MP(6, 256, 12, 0)
-        BOBA_MP(7, 512, 8, 0)
-        BOBA_MP(8, 128, 16, 0)
-        BOBA_MP(9, 256, 8, 1)
-        BOBA_MP(10, 256, 8, 2)
-        BOBA_MP(11, 256, 12, 1)
-        BOBA_MP(12, 512, 8, 1)
-        BOBA_MP(13, 256, 16, 1)
+        BOBA_MP(5, 256, 8, 0, false)
+        BOBA_MP(6, 256, 12, 0, false)
+        BOBA_MP(7, 512, 8, 0, false)
+        BOBA_MP(8, 128, 16, 0, false)
+        BOBA_MP(9, 256, 8, 1, false)
+        BOBA_MP(10, 256, 8, 2, false)
+        BOBA_MP(11, 256, 12, 1, false)
+        BOBA_MP(12, 512, 8, 1, false)
+        BOBA_MP(13, 256, 16, 1, false)
+        BOBA_MP(14, 256, 12, 3, true)
     }
 #undef BOBA_MP
     BOBA_TIMED("spmv.fixup", stream,
@@ -496,7 +528,7 @@ extern "C" boba_status_t boba_spmv_csr(const int64_t *row_ptr, const int32_t *co
     const uint32_t cap = (uint32_t)L.cap;
 
     const int tv = tuned_variant(kTuneSpmv, nnz);
-    // 0 auto, 1..4: LPR 4, 8, 16, 32; 5..13: merge path, shapes in kMpShapes
+    // 0 auto, 1..4: LPR 4, 8, 16, 32; 5..14: merge path, shapes in kMpShapes
     if (tv >= kMpFirst && tv <= kMpLast) {
         int2 *part = reinterpret_cast<int2 *>(b + L.mp_part);
         int32_t *crow = reinterpret_cast<int32_t *>(b + L.mp_crow);

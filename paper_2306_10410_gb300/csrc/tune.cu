@@ -32,7 +32,7 @@ constexpr int kClasses = 64;
 // variant must also stay within that of the default variant's fp32 result.
 constexpr double kSpmvTuneRelL2 = 1e-5;
 constexpr int kMaxDev = 64;
-constexpr int kVariants[kTuneKernels] = {8, 8, 9, 14, 10};   // first, relabel, batched, spmv, csr
+constexpr int kVariants[kTuneKernels] = {8, 8, 9, 15, 10};   // first, relabel, batched, spmv, csr
 const char *kNames[kTuneKernels] = {"first", "relabel", "batched", "spmv", "csr"};
 
 std::mutex g_tmu;

@@ -165,7 +165,7 @@ def test_full_size_rmat24_csr_spmv(boba):
     boba.load().boba_tune_set(boba.TUNE_CSR, w.m, -1)
 
 
-N_SPMV_VARIANTS = 14
+N_SPMV_VARIANTS = 15
 
 
 def check_spmv_all_variants(boba, gpu_csr, ora_csr, x, nnz):

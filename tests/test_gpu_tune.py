@@ -76,10 +76,10 @@ def test_tune_batched_and_spmv(boba):
     rp, col, val = boba.coo_to_csr(torch.from_numpy(I).cuda(), torch.from_numpy(J).cuda(), w.n)
     x = torch.from_numpy(synth.uniform_f32(w.n, seed=3)).cuda()
     ch = boba.tune_spmv(rp, col, val, x, reps=2)
-    assert 0 <= ch["spmv"] < 14
+    assert 0 <= ch["spmv"] < 15
     orp, ocol, oval = oracle.coo_to_csr(I, J, w.n)
     y64 = oracle.spmv_f64(orp, ocol, oval, x.cpu().numpy())
-    for v in range(14):                      # every variant within the bound
+    for v in range(15):                      # every variant within the bound
         boba.load().boba_tune_set(boba.TUNE_SPMV, col.numel(), v)
         y = boba.spmv(rp, col, val, x)
         boba.stream_status()
