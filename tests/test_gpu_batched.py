@@ -179,7 +179,7 @@ def test_size_limits(boba):
     assert boba.boba_reorder_batched_workspace_bytes(4096, 1 << 23, TEAM_MAX, 1 << 31, 1 << 28) > 0
 
 
-@pytest.mark.parametrize("mode", [1, 2, 4])
+@pytest.mark.parametrize("mode", [1, 2, 4, 6, 7, 8])
 def test_split_mode_takes_graphs_beyond_cluster_capacity(boba, mode):
     boba.boba_batched_set_mode(mode)           # the largest go to the global phases
     graphs = []
