@@ -142,17 +142,20 @@ def test_out_of_range_ids_reported(boba, mode):
     """An endpoint outside [0, n) of its own graph raises BOBA_ERR_ID_OUT_OF_RANGE
     and is written as -1; the other graphs of the batch come out unchanged.
     Graph 0 runs in one CTA; graph 1 has three slices, its bad IDs in
-    several of them and at both ends of its endpoint stream."""
+    several of them and at both ends of its endpoint stream.  Graph 0's odd
+    edge count leaves graph 1's arrays off a 16-byte boundary, and graph 1's
+    own count leaves a tail, so its first and last IDs are read one by one."""
     boba.boba_batched_set_mode(mode)
     graphs = []
-    for n, m, seed in ((3000, 40_000, 31), (2 * KCAP + 100, 600_000, 32),
+    for n, m, seed in ((3000, 40_001, 31), (2 * KCAP + 100, 600_003, 32),
                        (3 * KCAP + 7, 900_000, 33), (5000, 60_000, 34)):
         I, J = synth.rmat(int(np.ceil(np.log2(n))), m, seed=seed, n=n)
         graphs.append((I.copy(), J.copy(), n))
     n0, n1 = graphs[0][2], graphs[1][2]
     m1 = len(graphs[1][0])
     bad = {0: [(0, 17, n0), (1, 5, -1)],
-           1: [(0, 0, n1 + 7), (1, 999, -3), (0, 400_000, 1 << 30), (1, m1 - 1, n1)]}
+           1: [(0, 0, n1 + 7), (1, 999, -3), (0, 400_000, 1 << 30), (1, m1 - 1, n1),
+               (0, m1 - 1, -2)]}
     for g, items in bad.items():
         for side, e, v in items:
             graphs[g][side][e] = v
