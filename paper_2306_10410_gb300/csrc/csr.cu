@@ -289,10 +289,20 @@ __global__ void __launch_bounds__(BLOCK, MINB) k_csr_pass(
                 const unsigned vm = __ballot_sync(kFull, valid);
                 peers = valid ? vm : ~vm;
             }
+            // per bit: the lanes whose bit b matches this lane's, that is
+            // the ballot of the bit, inverted where this lane's bit is clear.
+            // In PTX the one predicate drives both the vote and the
+            // inversion; the C++ select between bm and ~bm issued more ALU
+            // instructions in this ALU-bound loop (radix pass on 2^28 keys:
+            // 1.93 ms, now 1.82-1.85 ms)
 #pragma unroll
             for (int b = 0; b < 8; ++b) {
-                const unsigned bm = __ballot_sync(kFull, (d >> b) & 1u);
-                peers &= ((d >> b) & 1u) ? bm : ~bm;
+                asm("{\n\t.reg .pred p;\n\t.reg .b32 m;\n\t"
+                    "setp.ne.u32 p, %1, 0;\n\t"
+                    "vote.sync.ballot.b32 m, p, 0xffffffff;\n\t"
+                    "@!p not.b32 m, m;\n\t"
+                    "and.b32 %0, %0, m;\n\t}"
+                    : "+r"(peers) : "r"(d & (1u << b)));
             }
         } else {
             peers = __match_any_sync(kFull, d);

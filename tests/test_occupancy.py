@@ -63,7 +63,9 @@ def test_radix_pass_register_budgets():
             if minb == 2:
                 assert spill <= 8, (name, spill)
             if prescan:                               # the default from 2^22 keys on
-                assert spill == 0, (name, spill)
+                # 4 bytes since the ranking's ballots moved to PTX, which
+                # measured 5 % faster with them than the spill-free C++ form
+                assert spill <= 4, (name, spill)
         else:
             assert spill <= 64, (name, spill)         # tuner-only shapes, timed by the tuner
     assert (512, 8, 1, 3) in shapes                   # the default: ballots, three blocks
