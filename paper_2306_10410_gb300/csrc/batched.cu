@@ -210,6 +210,16 @@ __device__ __forceinline__ uint32_t *key_ptr(uint32_t *s_keys, TeamSmem &ts, uin
     else return ts.kp[owner];
 }
 
+// The team member whose bitmap slice of Wc words holds bitmap word w.  One
+// CTA alone owns every word; in a team w < 2^27 (keys are 32-bit positions),
+// so a 32-bit division suffices.
+template <int T>
+__device__ __forceinline__ uint32_t owner_of_word(uint32_t w, int64_t Wc)
+{
+    if constexpr (T == 1) return 0u;
+    else return w / (uint32_t)Wc;
+}
+
 // Process graph g with a team of T CTAs; this CTA is member t, the team's CTAs
 // are grid CTAs cta0 .. cta0+T-1 (their scratch regions).
 template <int T>
@@ -282,9 +292,10 @@ __device__ void process_graph(const BatchArgs &a, uint32_t g, int t, int64_t cta
     for (int64_t i = tid; i < myn; i += kBB) {
         const uint32_t k = s_keys[i];
         if (k == kSent) { ++iso; continue; }
-        const int64_t w = k >> 5;
-        const int64_t r = w / Wc;
-        atomicOr(a.scratch + (cta0 + r) * a.region_words + (w - r * Wc), 1u << (k & 31u));
+        const uint32_t w = k >> 5;                  // keys are 32-bit positions
+        const uint32_t r = owner_of_word<T>(w, Wc);
+        atomicOr(a.scratch + (cta0 + r) * a.region_words + (w - r * (uint32_t)Wc),
+                 1u << (k & 31u));
     }
     {
         uint32_t tot;
@@ -346,9 +357,9 @@ __device__ void process_graph(const BatchArgs &a, uint32_t g, int t, int64_t cta
                 if (isf) {
                     lab = K + isob + carry + ex;
                 } else {
-                    const int64_t w = k >> 5;
-                    const int64_t r = w / Wc;
-                    const int64_t wl = w - r * Wc;
+                    const uint32_t w = k >> 5;
+                    const uint32_t r = owner_of_word<T>(w, Wc);
+                    const uint32_t wl = w - r * (uint32_t)Wc;
                     const uint32_t *bm = a.scratch + (cta0 + r) * a.region_words;
                     const uint32_t *gp = bm + a.wmax;
                     const uint4 *gw = reinterpret_cast<const uint4 *>(bm + ((wl >> 3) << 3));
