@@ -981,15 +981,14 @@ __device__ __forceinline__ void first_slice_stream(const int32_t *__restrict__ X
                         if (b0 + (uint32_t)u * kBB < q) vmax = max(vmax, (uint32_t)lane_of(w[u], j));
                 }
             }
+            // an endpoint outside the slice read 0, which no position is below
 #pragma unroll
             for (int u = h; u < h + kFirstSliceG; ++u) {
                 const uint32_t p = pb + 4u * (b0 + (uint32_t)u * kBB);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const uint32_t x = (uint32_t)lane_of(w[u], j) - base;
-                    if (x < cnt && cur[4 * (u - h) + j] > p + (uint32_t)j)
-                        atomicMin(&s_keys[x], p + (uint32_t)j);
-                }
+                for (int j = 0; j < 4; ++j)
+                    if (cur[4 * (u - h) + j] > p + (uint32_t)j)
+                        atomicMin(&s_keys[(uint32_t)lane_of(w[u], j) - base], p + (uint32_t)j);
             }
         }
     }
