@@ -253,36 +253,47 @@ __device__ void process_graph(const BatchArgs &a, uint32_t g, int t, int64_t cta
         bool bad = false;
         const int64_t P = 2 * m;
         const int64_t lo = P * t / T, hi = P * (t + 1) / T;
-        for (int64_t b0 = lo + tid; b0 < hi; b0 += (int64_t)kU * kBB) {
-            int32_t v[kU];
+        const int32_t *srcg = a.src + E0, *dstg = a.dst + E0;
+        // Idx: the type of the position indices.  32-bit indices save the
+        // second instruction of every 64-bit add and compare; they are used
+        // when no index of the sweep, counter steps included, can pass 2^32.
+        auto sweep = [&](auto idx_tag) {
+            using Idx = decltype(idx_tag);
+            const Idx hi_ = (Idx)hi, m_ = (Idx)m;
+            for (Idx b0 = (Idx)lo + (Idx)tid; b0 < hi_; b0 += (Idx)(kU * kBB)) {
+                int32_t v[kU];
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int64_t i = b0 + (int64_t)u * kBB;
-                v[u] = -1;
-                if (i < hi) v[u] = i < m ? __ldcs(a.src + E0 + i) : __ldcs(a.dst + E0 + (i - m));
-            }
-            uint32_t own[kU], li[kU], cur[kU];
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int64_t i = b0 + (int64_t)u * kBB;
-                // predicates rather than branches; one CTA owns every vertex
-                const bool ok = i < hi && (uint32_t)v[u] < nn;
-                bad |= i < hi && !ok;
-                if constexpr (T == 1) {
-                    own[u] = ok ? 0u : (uint32_t)kTeam;          // kTeam: "skip"
-                    li[u] = (uint32_t)v[u];
-                } else {
-                    own[u] = ok ? (uint32_t)v[u] / chunk : (uint32_t)kTeam;
-                    li[u] = (uint32_t)v[u] - own[u] * chunk;
+                for (int u = 0; u < kU; ++u) {
+                    const Idx i = b0 + (Idx)(u * kBB);
+                    v[u] = -1;
+                    if (i < hi_) v[u] = i < m_ ? __ldcs(srcg + i) : __ldcs(dstg + (i - m_));
                 }
-                cur[u] = ok ? key_ptr<T>(s_keys, ts, own[u])[li[u]] : 0u;
-            }
+                uint32_t own[kU], li[kU], cur[kU];
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const uint32_t i = (uint32_t)(b0 + (int64_t)u * kBB);
-                if (own[u] < kTeam && cur[u] > i) atomicMin(key_ptr<T>(s_keys, ts, own[u]) + li[u], i);
+                for (int u = 0; u < kU; ++u) {
+                    const Idx i = b0 + (Idx)(u * kBB);
+                    // predicates rather than branches; one CTA owns every vertex
+                    const bool ok = i < hi_ && (uint32_t)v[u] < nn;
+                    bad |= i < hi_ && !ok;
+                    if constexpr (T == 1) {
+                        own[u] = ok ? 0u : (uint32_t)kTeam;          // kTeam: "skip"
+                        li[u] = (uint32_t)v[u];
+                    } else {
+                        own[u] = ok ? (uint32_t)v[u] / chunk : (uint32_t)kTeam;
+                        li[u] = (uint32_t)v[u] - own[u] * chunk;
+                    }
+                    cur[u] = ok ? key_ptr<T>(s_keys, ts, own[u])[li[u]] : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const uint32_t i = (uint32_t)(b0 + (Idx)(u * kBB));
+                    if (own[u] < kTeam && cur[u] > i)
+                        atomicMin(key_ptr<T>(s_keys, ts, own[u]) + li[u], i);
+                }
             }
-        }
+        };
+        if (hi <= (int64_t)0xFFFFFFFFu - (int64_t)kU * kBB) sweep(uint32_t{});
+        else sweep(int64_t{});
         if (bad) raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
     }
     team_sync<T>(cl);
@@ -386,16 +397,19 @@ __device__ void process_graph(const BatchArgs &a, uint32_t g, int t, int64_t cta
     // flight per thread, all label reads, then the stores
     {
         constexpr int U2 = kU / 2;
-        const int64_t lo = m * t / T, hi = m * (t + 1) / T;
-        for (int64_t b0 = lo + tid; b0 < hi; b0 += (int64_t)U2 * kBB) {
+        // 32-bit edge indices: hi <= m < 2^31, so no counter step passes 2^32
+        const uint32_t lo = (uint32_t)(m * t / T), hi = (uint32_t)(m * (t + 1) / T);
+        const int32_t *srcg = a.src + E0, *dstg = a.dst + E0;
+        int32_t *sog = a.so + E0, *dog = a.dout + E0;
+        for (uint32_t b0 = lo + (uint32_t)tid; b0 < hi; b0 += (uint32_t)(U2 * kBB)) {
             int32_t v[kU];
 #pragma unroll
             for (int u = 0; u < U2; ++u) {
-                const int64_t e = b0 + (int64_t)u * kBB;
+                const uint32_t e = b0 + (uint32_t)(u * kBB);
                 v[2 * u] = v[2 * u + 1] = -1;
                 if (e < hi) {
-                    v[2 * u] = __ldcs(a.src + E0 + e);
-                    v[2 * u + 1] = __ldcs(a.dst + E0 + e);
+                    v[2 * u] = __ldcs(srcg + e);
+                    v[2 * u + 1] = __ldcs(dstg + e);
                 }
             }
             int32_t lab[kU];
@@ -411,12 +425,12 @@ __device__ void process_graph(const BatchArgs &a, uint32_t g, int t, int64_t cta
             }
 #pragma unroll
             for (int u = 0; u < U2; ++u) {
-                const int64_t e = b0 + (int64_t)u * kBB;
+                const uint32_t e = b0 + (uint32_t)(u * kBB);
                 if (e >= hi) continue;
                 if (lab[2 * u] < 0 || lab[2 * u + 1] < 0)
                     raise_status(a.status, BOBA_ERR_ID_OUT_OF_RANGE);
-                __stcs(a.so + E0 + e, lab[2 * u]);
-                __stcs(a.dout + E0 + e, lab[2 * u + 1]);
+                __stcs(sog + e, lab[2 * u]);
+                __stcs(dog + e, lab[2 * u + 1]);
             }
         }
     }
